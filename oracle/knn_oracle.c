@@ -1,0 +1,491 @@
+/*
+ * knn_oracle.c -- plain, slow, double-precision CPU oracle for the adaptive
+ * k-NN method (LeJeune, Baraniuk, Heckel, AISTATS 2019).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the CPU
+ * baseline of the benchmark; never by the product path. Shares no code with
+ * the CUDA library.
+ *
+ * Pieces and where they come from:
+ *   - Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+ *     "Parallel random numbers: as easy as 1, 2, 3", SC'11), written from the
+ *     published round function.
+ *   - coordinate draw: uniform index in [0, m) with replacement (Section 4,
+ *     sampled estimator).
+ *   - alpha(u): footnote form (Section 4), Lemma form (Lemma "probound",
+ *     Section 6) and the experiment form with C_alpha (Section 5).
+ *   - brute force: all distances then sort (Section 3).
+ *   - batched rounds: every undecided point gets the same number of new
+ *     samples per round; the elimination/acceptance rules are the batched
+ *     form of the LUCB indices (Eq. d_ind) and of the termination argument
+ *     (Eq. termination and the first paragraph of the proof of Theorem 1).
+ *   - sequential: Algorithm 1 as printed (two arms per iteration).
+ */
+#include "knn_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- Philox */
+
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+    /* Multipliers and Weyl key increments of Philox4x64 (SC'11, Table 2). */
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t hi0, lo0, hi1, lo1;
+        mulhilo64(M0, c0, &hi0, &lo0);
+        mulhilo64(M1, c2, &hi1, &lo1);
+        uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The s-th draw of a (query, point) pair: counter (s / 8, point, query, 0),
+ * key (seed, 0); the 256 output bits are eight 32-bit words (low half of
+ * each 64-bit word first) and word s mod 8 is scaled to [0, m) by
+ * floor(word * m / 2^32). */
+int32_t orc_coordinate(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
+                       uint64_t mask_p, uint64_t mask_q) {
+    uint64_t ctr[4] = {s >> 3, point & mask_p, qid & mask_q, 0};
+    uint64_t key[2] = {seed, 0};
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    unsigned w = (unsigned)(s & 7);
+    uint32_t word = (uint32_t)(out[w >> 1] >> (32 * (w & 1)));
+    return (int32_t)(((uint64_t)word * (uint64_t)(uint32_t)m) >> 32);
+}
+
+/* ----------------------------------------------------------------- alpha */
+
+double orc_alpha(int32_t form, double c_alpha, int64_t u, int64_t n, double delta) {
+    double uu = (double)u;
+    double dprime = delta / (double)n;
+    if (form == ORC_BOUND_FOOTNOTE) {
+        /* beta(u, delta') = log(1/delta') + 3 log log(1/delta') + 1.5 log(1 + log u) */
+        double beta = log(1.0 / dprime) + 3.0 * log(log(1.0 / dprime)) + 1.5 * log(1.0 + log(uu));
+        return sqrt(2.0 * beta / uu);
+    }
+    if (form == ORC_BOUND_LEMMA) {
+        /* beta(t, delta') = 2 log(125 log(1.12 t) / delta') */
+        double beta = 2.0 * log(125.0 * log(1.12 * uu) / dprime);
+        return sqrt(2.0 * beta / uu);
+    }
+    /* Section 5: sqrt(C_alpha log(1 + (1 + log u) n / delta) / u) */
+    return sqrt(c_alpha * log(1.0 + (1.0 + log(uu)) * (double)n / delta) / uu);
+}
+
+/* ----------------------------------------------------------- brute force */
+
+typedef struct { double v; int64_t i; } vi_t;
+
+static int cmp_vi(const void* a, const void* b) {
+    const vi_t* x = (const vi_t*)a;
+    const vi_t* y = (const vi_t*)b;
+    if (x->v < y->v) return -1;
+    if (x->v > y->v) return 1;
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+static double sqdist(const float* x, const float* q, int32_t m) {
+    double s = 0.0;
+    for (int32_t j = 0; j < m; ++j) {
+        double d = (double)x[j] - (double)q[j];
+        s += d * d;
+    }
+    return s;
+}
+
+void orc_exact_knn(const float* X, int64_t n, int32_t m, const float* q, int32_t k,
+                   int64_t* idx, double* dist) {
+    vi_t* a = (vi_t*)malloc(sizeof(vi_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        a[i].v = sqdist(X + (size_t)i * (size_t)m, q, m);
+        a[i].i = i;
+    }
+    qsort(a, (size_t)n, sizeof(vi_t), cmp_vi);
+    for (int32_t t = 0; t < k; ++t) {
+        idx[t] = t < n ? a[t].i : -1;
+        if (dist) dist[t] = t < n ? a[t].v : INFINITY;
+    }
+    free(a);
+}
+
+void orc_exact_knn_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                         int32_t k, int64_t* idx, double* dist, int32_t threads) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int32_t qi = 0; qi < nq; ++qi)
+        orc_exact_knn(X, n, m, Q + (size_t)qi * (size_t)m, k, idx + (size_t)qi * (size_t)k,
+                      dist ? dist + (size_t)qi * (size_t)k : NULL);
+}
+
+int32_t orc_max_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------- batched rounds */
+
+/* A bound value together with the magnitude (estimate + width) of the pair
+ * it belongs to; the magnitude scales the near-threshold band. */
+typedef struct { double v; double mag; } vm_t;
+
+static int cmp_vm(const void* a, const void* b) {
+    const vm_t* x = (const vm_t*)a;
+    const vm_t* y = (const vm_t*)b;
+    if (x->v < y->v) return -1;
+    if (x->v > y->v) return 1;
+    return (x->mag < y->mag) - (x->mag > y->mag); /* larger magnitude first among ties */
+}
+
+/* Decision that a log entry implies for round r: ACTIVE, ELIMINATED or
+ * ACCEPTED, or -1 when the entry says the pair was already gone. */
+static int logged_decision(int32_t code, int32_t r) {
+    int32_t rc = code >> 2, kind = code & 3;
+    if (rc > r) return ORC_ACTIVE;
+    if (rc == r) return kind;
+    return -1;
+}
+
+static int64_t round_samples(const orc_adaptive_params* p, int32_t r, int64_t Tcur) {
+    if (r == 0) return p->B0;
+    if (p->grow) return Tcur > p->B ? Tcur : p->B;
+    return p->B;
+}
+
+int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
+                     const orc_adaptive_params* p, const int32_t* replay,
+                     int64_t* out_idx, int32_t* code, double* S, int32_t* T,
+                     orc_adaptive_stats* st) {
+    const int32_t k = p->k, h = p->h;
+    const int64_t kh = (int64_t)k + h;
+    if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->B0 < 1 || p->B < 1)
+        return 1;
+    memset(st, 0, sizeof(*st));
+    for (int64_t t = 0; t < kh; ++t) out_idx[t] = -1;
+
+    if (n <= kh) { /* every point is a candidate: nothing to estimate */
+        for (int64_t i = 0; i < n; ++i) {
+            out_idx[i] = i;
+            if (code) code[i] = ORC_ACTIVE;
+            if (S) S[i] = 0.0;
+            if (T) T[i] = 0;
+        }
+        st->count = (int32_t)n;
+        st->term = 0;
+        return 0;
+    }
+
+    /* Affine normalisation of Section 3 (||x||_inf <= 1/2): with
+     * span = max - min over the data and the query, every sample
+     * (x_ij - x_j)^2 / span^2 lies in [0, 1]; bounds are used in raw units
+     * scaled by span^2. */
+    double lo = q[0], hi = q[0];
+    for (int32_t j = 0; j < m; ++j) {
+        if (q[j] < lo) lo = q[j];
+        if (q[j] > hi) hi = q[j];
+    }
+    for (size_t e = 0; e < (size_t)n * (size_t)m; ++e) {
+        if (X[e] < lo) lo = X[e];
+        if (X[e] > hi) hi = X[e];
+    }
+    const double span = hi - lo;
+    const double span2 = span * span;
+
+    unsigned char* status = (unsigned char*)malloc((size_t)n);
+    double* Sx = (double*)malloc(sizeof(double) * (size_t)n);
+    int32_t* Tx = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* cx = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    double* dh = (double*)malloc(sizeof(double) * (size_t)n); /* frozen estimate */
+    double* ub = (double*)malloc(sizeof(double) * (size_t)n); /* frozen UCB */
+    double* lb = (double*)malloc(sizeof(double) * (size_t)n); /* frozen LCB */
+    double* wd = (double*)malloc(sizeof(double) * (size_t)n); /* frozen width */
+    unsigned char* newst = (unsigned char*)malloc((size_t)n);
+    vm_t* su = (vm_t*)malloc(sizeof(vm_t) * (size_t)n);
+    vm_t* sl = (vm_t*)malloc(sizeof(vm_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) { status[i] = ORC_ACTIVE; Sx[i] = 0.0; Tx[i] = 0; cx[i] = 0; }
+
+    int64_t nact = n, nacc = 0, evals = 0;
+    double min_elim = INFINITY, min_elim_mag = 0.0;
+    int64_t Tcur = 0;
+    int32_t r = 0, term = 0;
+    for (;;) {
+        int64_t Br = round_samples(p, r, Tcur);
+        int exact = (Tcur + Br >= m);
+        int64_t Tn = exact ? m : Tcur + Br;
+        /* Sample step (Algorithm 1 update, batched): every active point
+         * gets draws Tcur .. Tn-1, or its exact distance when the count
+         * would reach m ("If T = m, compute the distance exactly"). */
+        for (int64_t i = 0; i < n; ++i) {
+            if (status[i] != ORC_ACTIVE) continue;
+            const float* xi = X + (size_t)i * (size_t)m;
+            if (exact) {
+                Sx[i] = sqdist(xi, q, m);
+            } else {
+                for (int64_t t = Tcur; t < Tn; ++t) {
+                    int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, m, p->mask_p, p->mask_q);
+                    double d = (double)xi[j] - (double)q[j];
+                    Sx[i] += d * d;
+                }
+            }
+            Tx[i] = (int32_t)Tn;
+        }
+        evals += nact * (exact ? (int64_t)m : Br);
+        const double w = exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta);
+
+        /* Bounds of the non-eliminated points: current ones for active
+         * points, frozen ones for accepted points. */
+        int64_t cnt = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (status[i] == ORC_ACTIVE) {
+                double d = Sx[i] / (double)Tn;
+                su[cnt].v = d + w; su[cnt].mag = d + w;
+                sl[cnt].v = d - w; sl[cnt].mag = d + w;
+                ++cnt;
+            } else if (status[i] == ORC_ACCEPTED) {
+                su[cnt].v = ub[i]; su[cnt].mag = dh[i] + wd[i];
+                sl[cnt].v = lb[i]; sl[cnt].mag = dh[i] + wd[i];
+                ++cnt;
+            }
+        }
+        qsort(su, (size_t)cnt, sizeof(vm_t), cmp_vm);
+        qsort(sl, (size_t)cnt, sizeof(vm_t), cmp_vm);
+        /* tau_U: k-th smallest UCB (the batched q1 of Eq. d_ind);
+         * tau_L: (k+1)-th smallest LCB, or a smaller frozen LCB of an
+         * eliminated point (the batched q2). */
+        const double tauU = su[k - 1].v, tauU_mag = su[k - 1].mag;
+        double tauL = sl[k].v, tauL_mag = sl[k].mag;
+        if (min_elim < tauL) { tauL = min_elim; tauL_mag = min_elim_mag; }
+
+        /* Decide: a point whose LCB exceeds tau_U has k points certainly
+         * closer, so it is not among the k nearest; a point whose UCB is
+         * below tau_L is closer than n-k points, so it is among them. */
+        double round_min = INFINITY, round_min_mag = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            newst[i] = status[i];
+            if (status[i] != ORC_ACTIVE) continue;
+            double d = Sx[i] / (double)Tn;
+            double U = d + w, L = d - w, mag = d + w;
+            int o = (L > tauU) ? ORC_ELIMINATED : ((U < tauL) ? ORC_ACCEPTED : ORC_ACTIVE);
+            if (replay) {
+                int nearU = fabs(L - tauU) <= p->tol * (mag + tauU_mag);
+                int nearL = fabs(U - tauL) <= p->tol * (mag + tauL_mag);
+                int nr = nearU || nearL;
+                if (nr) st->near++;
+                int g = logged_decision(replay[i], r);
+                if (g < 0) {
+                    st->log_inconsistent++;
+                } else if (g != o) {
+                    if (nr) st->near_disagree++; else st->mismatch++;
+                    o = g;
+                }
+            }
+            if (o == ORC_ELIMINATED) {
+                newst[i] = ORC_ELIMINATED;
+                cx[i] = 4 * r + ORC_ELIMINATED;
+                dh[i] = d; lb[i] = L; ub[i] = U; wd[i] = w;
+                if (L < round_min) { round_min = L; round_min_mag = mag; }
+            } else if (o == ORC_ACCEPTED) {
+                newst[i] = ORC_ACCEPTED;
+                cx[i] = 4 * r + ORC_ACCEPTED;
+                dh[i] = d; lb[i] = L; ub[i] = U; wd[i] = w;
+            }
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (status[i] == ORC_ACTIVE && newst[i] != ORC_ACTIVE) {
+                --nact;
+                if (newst[i] == ORC_ACCEPTED) ++nacc;
+            }
+            status[i] = newst[i];
+        }
+        if (round_min < min_elim) { min_elim = round_min; min_elim_mag = round_min_mag; }
+        Tcur = Tn;
+        /* Termination (batched form of Eq. termination). */
+        if (nact + nacc <= kh) term = 1;
+        else if (nacc >= k) term = 2;
+        else if (exact) term = 3;
+        if (term) break;
+        ++r;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (status[i] == ORC_ACTIVE) { cx[i] = 4 * r + ORC_ACTIVE; dh[i] = Sx[i] / (double)Tx[i]; }
+    if (replay)
+        for (int64_t i = 0; i < n; ++i)
+            if ((replay[i] >> 2) > r || ((replay[i] & 3) == ORC_ACTIVE && (replay[i] >> 2) != r))
+                st->log_inconsistent++;
+
+    /* Output: accepted points by (estimate, index), then active points by
+     * (estimate, index), at most k+h (the set S-hat of Algorithm 1). */
+    vi_t* acc = (vi_t*)malloc(sizeof(vi_t) * (size_t)(nacc > 0 ? nacc : 1));
+    vi_t* act = (vi_t*)malloc(sizeof(vi_t) * (size_t)(nact > 0 ? nact : 1));
+    int64_t na = 0, nb = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (status[i] == ORC_ACCEPTED) { acc[na].v = dh[i]; acc[na].i = i; ++na; }
+        else if (status[i] == ORC_ACTIVE) { act[nb].v = dh[i]; act[nb].i = i; ++nb; }
+    }
+    qsort(acc, (size_t)na, sizeof(vi_t), cmp_vi);
+    qsort(act, (size_t)nb, sizeof(vi_t), cmp_vi);
+    int64_t c = 0;
+    for (int64_t t = 0; t < na && c < kh; ++t) out_idx[c++] = acc[t].i;
+    for (int64_t t = 0; t < nb && c < kh; ++t) out_idx[c++] = act[t].i;
+
+    st->evals = evals;
+    st->rounds = r + 1;
+    st->count = (int32_t)c;
+    st->term = term;
+    if (code) memcpy(code, cx, sizeof(int32_t) * (size_t)n);
+    if (S) memcpy(S, Sx, sizeof(double) * (size_t)n);
+    if (T) memcpy(T, Tx, sizeof(int32_t) * (size_t)n);
+    free(acc); free(act);
+    free(status); free(Sx); free(Tx); free(cx); free(dh); free(ub); free(lb); free(wd);
+    free(newst); free(su); free(sl);
+    return 0;
+}
+
+int32_t orc_adaptive_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                           const orc_adaptive_params* p, const int32_t* replay,
+                           int64_t* out_idx, int32_t* codes, double* S, int32_t* T,
+                           orc_adaptive_stats* st, int32_t threads) {
+    const int64_t kh = (int64_t)p->k + p->h;
+    int32_t bad = 0;
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(|: bad)
+#endif
+    for (int32_t qi = 0; qi < nq; ++qi) {
+        orc_adaptive_params pq = *p;
+        pq.qid = p->qid + (uint64_t)qi;
+        size_t off = (size_t)qi * (size_t)n;
+        bad |= orc_adaptive(X, n, m, Q + (size_t)qi * (size_t)m, &pq,
+                            replay ? replay + off : NULL, out_idx + (size_t)qi * (size_t)kh,
+                            codes ? codes + off : NULL, S ? S + off : NULL, T ? T + off : NULL,
+                            st + qi);
+    }
+    return bad;
+}
+
+/* ---------------------------------------------------- Algorithm 1 as printed */
+
+int32_t orc_sequential(const float* X, int64_t n, int32_t m, const float* q,
+                       const orc_adaptive_params* p, int64_t max_iter,
+                       int64_t* out_idx, int64_t* out_evals, int64_t* out_iters) {
+    const int32_t k = p->k, h = p->h;
+    const int64_t kh = (int64_t)k + h;
+    if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0)) return 1;
+    for (int64_t t = 0; t < kh; ++t) out_idx[t] = -1;
+    *out_evals = 0;
+    *out_iters = 0;
+    if (n <= kh) {
+        for (int64_t i = 0; i < n; ++i) out_idx[i] = i;
+        return 0;
+    }
+    double lo = q[0], hi = q[0];
+    for (int32_t j = 0; j < m; ++j) { if (q[j] < lo) lo = q[j]; if (q[j] > hi) hi = q[j]; }
+    for (size_t e = 0; e < (size_t)n * (size_t)m; ++e) { if (X[e] < lo) lo = X[e]; if (X[e] > hi) hi = X[e]; }
+    const double span2 = (hi - lo) * (hi - lo);
+
+    double* sum = (double*)malloc(sizeof(double) * (size_t)n);
+    double* est = (double*)malloc(sizeof(double) * (size_t)n);
+    double* al = (double*)malloc(sizeof(double) * (size_t)n);
+    int64_t* Tn = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t* perm = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t evals = 0;
+
+    /* Initialisation: one sample per point. */
+    for (int64_t i = 0; i < n; ++i) {
+        const float* xi = X + (size_t)i * (size_t)m;
+        if (m == 1) { /* one sample is the whole distance */
+            sum[i] = sqdist(xi, q, m); Tn[i] = 1; est[i] = sum[i]; al[i] = 0.0; evals += 1;
+        } else {
+            int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)i, 0, m, p->mask_p, p->mask_q);
+            double d = (double)xi[j] - (double)q[j];
+            sum[i] = d * d; Tn[i] = 1; est[i] = sum[i];
+            al[i] = span2 * orc_alpha(p->bound, p->c_alpha, 1, n, p->delta);
+            evals += 1;
+        }
+        perm[i] = i;
+    }
+    /* Sort the permutation by (estimate, index); insertion sort keeps it
+     * ordered cheaply as only two estimates change per iteration. */
+    for (int64_t a = 1; a < n; ++a) {
+        int64_t v = perm[a], b = a - 1;
+        while (b >= 0 && (est[perm[b]] > est[v] || (est[perm[b]] == est[v] && perm[b] > v))) {
+            perm[b + 1] = perm[b]; --b;
+        }
+        perm[b + 1] = v;
+    }
+    int64_t it = 0;
+    for (; it < max_iter; ++it) {
+        /* q1: largest UCB among the k smallest estimates. */
+        int64_t q1 = perm[0];
+        for (int64_t a = 0; a < k; ++a) {
+            int64_t i = perm[a];
+            if (est[i] + al[i] > est[q1] + al[q1]) q1 = i;
+        }
+        /* q2: smallest LCB among ranks k+h+1 .. n. */
+        int64_t q2 = perm[kh];
+        for (int64_t a = kh; a < n; ++a) {
+            int64_t i = perm[a];
+            if (est[i] - al[i] < est[q2] - al[q2]) q2 = i;
+        }
+        if (est[q1] + al[q1] <= est[q2] - al[q2]) break; /* Eq. termination */
+        /* b2: largest width among q2 and the middle ranks k+1 .. k+h (Eq. blowbupdef). */
+        int64_t b2 = q2;
+        for (int64_t a = k; a < kh; ++a) {
+            int64_t i = perm[a];
+            if (al[i] > al[b2]) b2 = i;
+        }
+        int64_t upd[2] = {q1, b2};
+        for (int u = 0; u < 2; ++u) {
+            int64_t l = upd[u];
+            if (Tn[l] >= m) continue; /* already exact */
+            const float* xl = X + (size_t)l * (size_t)m;
+            int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)l, (uint64_t)Tn[l], m, p->mask_p, p->mask_q);
+            double d = (double)xl[j] - (double)q[j];
+            sum[l] += d * d;
+            Tn[l] += 1;
+            evals += 1;
+            if (Tn[l] == m) {
+                est[l] = sqdist(xl, q, m) / (double)m;
+                al[l] = 0.0;
+                evals += m;
+            } else {
+                est[l] = sum[l] / (double)Tn[l];
+                al[l] = span2 * orc_alpha(p->bound, p->c_alpha, Tn[l], n, p->delta);
+            }
+        }
+        /* Restore the order (insertion sort on a nearly sorted array). */
+        for (int64_t a = 1; a < n; ++a) {
+            int64_t v = perm[a], b = a - 1;
+            while (b >= 0 && (est[perm[b]] > est[v] || (est[perm[b]] == est[v] && perm[b] > v))) {
+                perm[b + 1] = perm[b]; --b;
+            }
+            perm[b + 1] = v;
+        }
+    }
+    for (int64_t t = 0; t < kh; ++t) out_idx[t] = perm[t];
+    *out_evals = evals;
+    *out_iters = it;
+    free(sum); free(est); free(al); free(Tn); free(perm);
+    return it >= max_iter ? 2 : 0;
+}

@@ -1,0 +1,306 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself (numpy's Philox and sort, closed-form special cases, brute force,
+Theorem 1's guarantee, the coherent example of Section 4.2)."""
+
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1902_09465_gb300 import synth
+
+FULL = (1 << 64) - 1
+
+
+# ------------------------------------------------------------------ Philox
+
+def _numpy_philox(ctr, key):
+    """Philox4x64-10 block for counter `ctr` from numpy's bit generator, which
+    increments its 256-bit counter before producing a block."""
+    c = sum(int(v) << (64 * i) for i, v in enumerate(ctr))
+    c = (c - 1) % (1 << 256)
+    pre = np.array([(c >> (64 * i)) & FULL for i in range(4)], dtype=np.uint64)
+    g = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=pre)
+    return g.random_raw(4).astype(np.uint64)
+
+
+@pytest.mark.parametrize("ctr,key", [
+    ([0, 0, 0, 0], [0, 0]),
+    ([1, 0, 0, 0], [0, 0]),
+    ([FULL, FULL, FULL, FULL], [FULL, FULL]),
+    ([0x243F6A8885A308D3, 0x13198A2E03707344, 0xA4093822299F31D0, 0x082EFA98EC4E6C89],
+     [0x452821E638D01377, 0xBE5466CF34E90C6C]),
+    ([7, 123456, 42, 0], [2019, 0]),
+])
+def test_philox_matches_numpy(ctr, key):
+    np.testing.assert_array_equal(oracle.philox4x64_10(ctr, key), _numpy_philox(ctr, key))
+
+
+def test_coordinates_follow_numpy_stream():
+    seed, qid, point, m = 99, 3, 12345, 784
+    for s in range(0, 40):
+        blk = _numpy_philox([s >> 3, point, qid, 0], [seed, 0])
+        w = s & 7
+        word = (int(blk[w >> 1]) >> (32 * (w & 1))) & 0xFFFFFFFF
+        assert oracle.coordinate(seed, qid, point, s, m) == (word * m) >> 32
+
+
+def test_coordinates_uniform():
+    m = 97
+    js = np.array([oracle.coordinate(5, 1, 2, s, m) for s in range(20000)])
+    assert js.min() >= 0 and js.max() < m
+    counts = np.bincount(js, minlength=m)
+    chi2 = ((counts - len(js) / m) ** 2 / (len(js) / m)).sum()
+    assert chi2 < stats.chi2.ppf(0.9999, m - 1)
+
+
+def test_share_mask_makes_coordinates_common():
+    a = [oracle.coordinate(1, 0, 10, s, 500, mask_p=0) for s in range(32)]
+    b = [oracle.coordinate(1, 0, 77, s, 500, mask_p=0) for s in range(32)]
+    c = [oracle.coordinate(1, 0, 77, s, 500) for s in range(32)]
+    assert a == b and a != c
+
+
+# ------------------------------------------------------------------- alpha
+
+def test_alpha_footnote_special_value():
+    # delta' = exp(-e): log(1/delta') = e and log log(1/delta') = 1; at u = 1
+    # the last term vanishes, so beta = e + 3 and alpha = sqrt(2 (e + 3)).
+    d = math.exp(-math.e)
+    assert oracle.alpha("footnote", 1, 1, d) == pytest.approx(math.sqrt(2 * (math.e + 3)), rel=1e-12)
+
+
+def test_alpha_lemma_special_value():
+    # 125 log(1.12) / delta' = e^10 gives beta(1) = 20 and alpha(1) = sqrt(40).
+    d = 125 * math.log(1.12) / math.exp(10)
+    assert oracle.alpha("lemma", 1, 1, d) == pytest.approx(math.sqrt(40.0), rel=1e-12)
+
+
+def test_alpha_exp_special_value():
+    # n / delta = e^5 - 1 gives log(1 + n/delta) = 5 at u = 1.
+    d = 1.0 / (math.exp(5) - 1)
+    for c in (1.0, 0.01):
+        assert oracle.alpha("exp", 1, 1, d, c_alpha=c) == pytest.approx(math.sqrt(5 * c), rel=1e-12)
+
+
+@pytest.mark.parametrize("form", ["footnote", "lemma", "exp"])
+def test_alpha_decreasing_and_lil_rate(form):
+    a = np.array([oracle.alpha(form, u, 1000, 0.01) for u in range(1, 5000)])
+    assert np.all(np.diff(a) < 0)
+    # alpha(u) sqrt(u) grows at most like sqrt(log log u): doubly logarithmic.
+    g = a * np.sqrt(np.arange(1, 5000))
+    assert g[-1] / g[10] < 1.5
+
+
+def test_alpha_lemma_coverage():
+    """Lemma probound: with prob >= 1 - delta' the running mean of [0,1]
+    samples stays within alpha(t) of its mean for every t. Bernoulli arms."""
+    rng = np.random.default_rng(0)
+    n_arms, horizon, delta = 400, 3000, 0.04
+    ts = np.arange(1, horizon + 1)
+    for form in ("footnote", "lemma"):
+        al = np.array([oracle.alpha(form, t, 1, delta) for t in ts])
+        viol = 0
+        for p in (0.5, 0.1):
+            x = rng.random((n_arms, horizon)) < p
+            means = np.cumsum(x, axis=1) / ts
+            viol += np.any(np.abs(means - p) > al, axis=1).sum()
+        assert viol <= stats.binom.ppf(0.999, 2 * n_arms, delta)
+
+
+# ------------------------------------------------------------- brute force
+
+def test_exact_knn_matches_numpy_with_ties():
+    rng = np.random.default_rng(1)
+    for trial in range(20):
+        n, m, k = int(rng.integers(5, 17)), int(rng.integers(1, 9)), int(rng.integers(1, 5))
+        X = rng.integers(-2, 3, size=(n, m)).astype(np.float32)   # many exact ties
+        q = rng.integers(-2, 3, size=(1, m)).astype(np.float32)
+        d = ((X.astype(np.float64) - q) ** 2).sum(1)
+        order = np.lexsort((np.arange(n), d))[:k]
+        idx, dist = oracle.exact_knn(X, q, k)
+        np.testing.assert_array_equal(idx[0], order)
+        np.testing.assert_allclose(dist[0], d[order], rtol=0, atol=0)
+
+
+# --------------------------------------------------------------- adaptive
+
+def _params(**kw):
+    base = dict(k=5, delta=0.01, bound="exp", c_alpha=1e-4, B0=16, B=16, grow=0, seed=0)
+    base.update(kw)
+    return oracle.make_params(**base)
+
+
+def test_all_coordinates_gives_exact_result():
+    """T = m means the distance is computed exactly (Algorithm 1)."""
+    X, Q, _ = synth.gaussian_planted(300, 24, 4, seed=3)
+    p = _params(k=4, B0=24, bound="footnote")
+    r = oracle.adaptive(X, Q, p)
+    d = ((X.astype(np.float64) - Q[0].astype(np.float64)) ** 2).sum(1)
+    st = r["stats"][0]
+    assert st["evals"] == 300 * 24 and st["rounds"] == 1
+    np.testing.assert_allclose(r["S"][0], d, rtol=1e-12)
+    true8 = np.lexsort((np.arange(300), d))[:8]
+    assert set(r["idx"][0][: st["count"]]) <= set(true8) | set(r["idx"][0])
+    assert set(np.lexsort((np.arange(300), d))[:4]) <= set(r["idx"][0][: st["count"]])
+
+
+def test_estimates_are_sample_means_of_drawn_coordinates():
+    """S is the sum of squared differences at the coordinates numpy's Philox
+    stream selects, for T samples (sampled estimator, Section 4)."""
+    X, Q, _ = synth.gaussian_planted(40, 64, 3, seed=4)
+    p = _params(k=3, B0=8, B=8, c_alpha=1e-3, seed=11)
+    r = oracle.adaptive(X, Q, p)
+    for i in range(40):
+        T = int(r["T"][0, i])
+        if T >= 64:
+            exp = ((X[i].astype(np.float64) - Q[0]) ** 2).sum()
+        else:
+            js = []
+            for s in range(T):
+                blk = _numpy_philox([s >> 3, i, 0, 0], [11, 0])
+                w = s & 7
+                js.append((((int(blk[w >> 1]) >> (32 * (w & 1))) & 0xFFFFFFFF) * 64) >> 32)
+            js = np.array(js)
+            exp = ((X[i, js].astype(np.float64) - Q[0, js].astype(np.float64)) ** 2).sum()
+        assert r["S"][0, i] == pytest.approx(exp, rel=1e-12, abs=0)
+
+
+def test_schedule_does_not_change_the_stream():
+    X, Q, _ = synth.gaussian_planted(500, 128, 5, seed=5)
+    a = oracle.adaptive(X, Q, _params(B0=16, B=16))
+    b = oracle.adaptive(X, Q, _params(B0=8, B=8))
+    same = a["T"][0] == b["T"][0]
+    assert same.sum() > 50
+    np.testing.assert_array_equal(a["S"][0][same], b["S"][0][same])
+
+
+def test_size_and_state_invariants():
+    rng = np.random.default_rng(7)
+    for trial in range(12):
+        n, m, k = int(rng.integers(30, 400)), int(rng.integers(8, 200)), int(rng.integers(1, 6))
+        h = int(rng.integers(0, 6))
+        X, Q, _ = synth.gaussian_planted(n, m, k, seed=100 + trial)
+        p = _params(k=k, h=h, B0=int(rng.integers(1, 20)), B=int(rng.integers(1, 20)), grow=trial % 2,
+                    c_alpha=float(10 ** rng.uniform(-5, -2)), seed=trial)
+        r = oracle.adaptive(X, Q, p)
+        st = r["stats"][0]
+        kind = r["code"][0] & 3
+        assert st["count"] <= k + h
+        out = r["idx"][0][: st["count"]]
+        assert len(set(out)) == len(out) and np.all(r["idx"][0][st["count"]:] == -1)
+        # candidates are exactly the accepted and still-active points (truncated)
+        live = np.flatnonzero(kind != oracle.ELIMINATED)
+        assert set(out) <= set(live)
+        if len(live) <= k + h:
+            assert set(out) == set(live)
+        assert (kind == oracle.ACCEPTED).sum() < 2 * k
+        # evaluation count = samples drawn + m per exact distance; an exact
+        # point also drew every sample of the rounds before its exact round
+        T = r["T"][0]
+        tb, rr = 0, 0
+        while True:
+            br = p.B0 if rr == 0 else (max(p.B, tb) if p.grow else p.B)
+            if tb + br >= m:
+                break
+            tb, rr = tb + br, rr + 1
+        ex = T == m
+        assert st["evals"] == T[~ex].sum() + ex.sum() * (tb + m)
+
+
+def test_trivial_when_n_le_k_plus_h():
+    X, Q, _ = synth.gaussian_planted(9, 16, 4, seed=1)
+    r = oracle.adaptive(X, Q, _params(k=4, h=5))
+    assert r["stats"][0]["evals"] == 0
+    assert list(r["idx"][0]) == list(range(9))
+
+
+def test_degenerate_identical_points():
+    X = np.ones((50, 16), dtype=np.float32)
+    q = np.ones((1, 16), dtype=np.float32)
+    r = oracle.adaptive(X, q, _params(k=3, h=2, bound="footnote"))
+    st = r["stats"][0]
+    assert st["term"] == 3 and st["count"] == 5
+    assert list(r["idx"][0]) == [0, 1, 2, 3, 4]
+
+
+def test_coherent_axis_gives_no_savings():
+    """Section 4.2: points on one axis need m samples each (theory bound)."""
+    X, q = synth.coherent_axis(200, 256, axis=17, seed=2)
+    p = _params(k=5, bound="footnote", B0=16, B=16)
+    r = oracle.adaptive(X, q, p)
+    st = r["stats"][0]
+    rounds = r["code"][0] >> 2
+    assert st["rounds"] == 16                            # 15 sampled rounds, then the exact one
+    assert np.all(rounds == st["rounds"] - 1)          # nothing decided before the exact round
+    assert st["evals"] == 200 * (240 + 256)
+    ti, _ = oracle.exact_knn(X, q, 5)
+    assert set(ti[0]) <= set(r["idx"][0][: st["count"]])
+
+
+def test_containment_rate_binary_data():
+    """Theorem 1: the returned set contains the k nearest neighbours with
+    probability >= 1 - delta. Binary +-1/2 data (Theorem 2's model), where a
+    sample is an exact Bernoulli draw of the normalised distance."""
+    trials, delta, k = 150, 0.05, 3
+    fails, saved = 0, 0
+    for t in range(trials):
+        X, q, near = synth.binary_half(150, 2048, k, 0.05, 0.45, seed=1000 + t)
+        p = oracle.make_params(k, delta=delta, bound="footnote", B0=32, B=32, grow=1, seed=t)
+        r = oracle.adaptive(X, q, p)
+        st = r["stats"][0]
+        ti, _ = oracle.exact_knn(X, q, k)
+        fails += not set(ti[0]) <= set(r["idx"][0][: st["count"]])
+        saved += st["evals"] < 150 * 2048
+    assert fails <= stats.binom.ppf(0.999, trials, delta)
+    assert saved >= 0.9 * trials    # the bound is not saturated here: adaptivity must pay
+
+
+def test_easy_instance_recall_and_savings():
+    X, Q, planted = synth.gaussian_planted(2000, 256, 5, seed=0)
+    ti, _ = oracle.exact_knn(X, Q, 5)
+    r = oracle.adaptive(X, Q, _params(k=5, c_alpha=1e-4))
+    st = r["stats"][0]
+    assert set(ti[0]) <= set(r["idx"][0][: st["count"]])
+    assert st["evals"] < 0.15 * 2000 * 256
+
+
+def test_replay_of_own_log_is_clean_and_detects_a_planted_error():
+    X, Q, _ = synth.gaussian_planted(800, 128, 5, seed=9)
+    p = _params(c_alpha=3e-4)
+    r = oracle.adaptive(X, Q, p)
+    rr = oracle.adaptive(X, Q, p, replay=r["code"])
+    s = rr["stats"][0]
+    assert s["mismatch"] == 0 and s["near_disagree"] == 0 and s["log_inconsistent"] == 0
+    np.testing.assert_array_equal(rr["code"], r["code"])
+    bad = r["code"].copy()
+    i = int(np.flatnonzero((bad[0] & 3) == oracle.ELIMINATED)[0])
+    bad[0, i] = (bad[0, i] & ~3) | oracle.ACCEPTED           # flip one logged decision
+    rb = oracle.adaptive(X, Q, p, replay=bad)
+    assert rb["stats"][0]["mismatch"] + rb["stats"][0]["near_disagree"] >= 1
+
+
+# ------------------------------------------------------ Algorithm 1 (sequential)
+
+def test_sequential_algorithm_contains_knn():
+    fails = 0
+    for t in range(20):
+        X, q, near = synth.binary_half(60, 256, 3, 0.05, 0.45, seed=t)
+        p = oracle.make_params(3, delta=0.05, bound="footnote", seed=t)
+        idx, evals, iters = oracle.sequential(X, q, p)
+        ti, _ = oracle.exact_knn(X, q, 3)
+        assert len(set(idx)) == 6
+        fails += not set(ti[0]) <= set(idx)
+        assert evals <= 60 * 2 * 256
+    assert fails <= 3
+
+
+def test_sequential_and_batched_same_order_of_cost():
+    X, q, _ = synth.binary_half(100, 1024, 3, 0.05, 0.45, seed=77)
+    p = oracle.make_params(3, delta=0.05, bound="footnote", B0=8, B=8, grow=1, seed=1)
+    _, ev_seq, _ = oracle.sequential(X, q, p)
+    r = oracle.adaptive(X, q, p)
+    ev_bat = r["stats"][0]["evals"]
+    assert 0.1 < ev_bat / ev_seq < 10
