@@ -1,0 +1,148 @@
+/*
+ * knn_gb300.h -- C ABI of the GB300 (sm_103a) adaptive k-nearest-neighbour
+ * library.
+ *
+ * Method: LeJeune, Baraniuk, Heckel, "Adaptive Estimation for Approximate
+ * k-Nearest-Neighbor Computations" (AISTATS 2019). Given points X (n x m) and a
+ * query x, return a set of size at most k+h that contains the k nearest
+ * neighbours of x in squared l2 distance (Section 3), by estimating the
+ * normalised distances d_i = ||x - x_i||^2 / m from uniformly sampled
+ * coordinates (Section 4) and discarding points whose confidence intervals
+ * separate them from the k closest (Algorithm 1, Eq. d_ind, Eq. termination).
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers unless stated; the caller owns
+ *     them. Matrices are row-major and densely packed (row stride = m).
+ *   - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream). Argument errors are detected on the host before any
+ *     launch and returned; launch failures return KNN_ECUDA. Nothing is
+ *     thrown across the ABI. knn_last_error() gives a message for the last
+ *     failing call on the calling thread.
+ *   - `workspace` is device scratch of at least the size the matching
+ *     *_workspace_size function returns (256-byte aligned). If `workspace` is
+ *     NULL the library allocates it stream-ordered (cudaMallocAsync) and frees
+ *     it stream-ordered after the work.
+ *   - Limits: 1 <= m <= 16384, 1 <= k, k + h <= 1024, n < 2^31.
+ */
+#ifndef KNN_GB300_H
+#define KNN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KNN_OK = 0,
+    KNN_EINVAL = 1,      /* invalid argument (sizes, delta, options, alignment) */
+    KNN_ENOMEM = 2,      /* workspace too small, or allocation failed */
+    KNN_ECUDA = 3,       /* a CUDA runtime call or launch failed */
+    KNN_EUNSUPPORTED = 4 /* the device is not sm_103 / feature not built */
+} knn_status;
+
+/* Confidence-bound forms alpha(u) (normalised units):
+ *   FOOTNOTE  sqrt(2 beta(u, delta/n) / u), beta = log(1/d') + 3 log log(1/d') + 1.5 log(1 + log u)
+ *             (Section 4, footnote to the definition of alpha; needs delta/n < 1/e)
+ *   LEMMA     sqrt(2 beta / u), beta = 2 log(125 log(1.12 u) / d'), d' = delta/n
+ *             (Lemma "probound", Section 6)
+ *   EXP       sqrt(C_alpha log(1 + (1 + log u) n / delta) / u)   (Section 5)       */
+typedef enum { KNN_BOUND_FOOTNOTE = 0, KNN_BOUND_LEMMA = 1, KNN_BOUND_EXP = 2 } knn_bound;
+
+/* Options of knn_adaptive. Fill with knn_opts_default() and change fields. */
+typedef struct {
+    int32_t h;          /* extra set size: returned set has at most k+h points; -1 means h = k */
+    int32_t bound;      /* knn_bound */
+    double c_alpha;     /* C_alpha of the EXP form */
+    int32_t B0;         /* coordinates sampled per point in round 0 (>= 1) */
+    int32_t B;          /* coordinates per point in later rounds (>= 1) */
+    int32_t grow;       /* 0: B per round; 1: max(B, T) per round (T doubles) */
+    uint64_t qid_base;  /* query i of the batch draws coordinates with query id qid_base + i */
+    uint64_t mask_p;    /* point field mask of the Philox counter (all ones: independent draws) */
+    uint64_t mask_q;    /* query field mask of the Philox counter (all ones: independent draws) */
+    int32_t threads;    /* threads per CTA of the round-loop kernel (0: library default) */
+    int32_t max_ctas;   /* cap on resident CTAs of the round-loop kernel (0: all that fit) */
+} knn_opts;
+
+void knn_opts_default(knn_opts* opts);
+
+/* Bytes of device scratch knn_adaptive needs for these sizes/options. */
+size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts);
+
+/*
+ * knn_adaptive -- the batched adaptive rounds (the hot path).
+ *
+ * For every query q (row q of Q, nq x m) independently:
+ *   round r draws B_r new coordinates j ~ U[0, m) for every still-active
+ *   point i (Philox4x64-10, key (seed, 0), counter (s/8, i & mask_p,
+ *   (qid_base+q) & mask_q, 0), 32-bit word s mod 8 scaled by floor(w m / 2^32),
+ *   s = 0,1,2,... the point's sample number); sums (X[i,j] - Q[q,j])^2 into a
+ *   running FP32 sum S_i (Kahan-compensated), or computes the exact distance
+ *   once T + B_r >= m ("If T = m, compute exactly", Algorithm 1);
+ *   with span = max(X, Q[q]) - min(X, Q[q]) (the normalisation of Section 3)
+ *   forms UCB/LCB = S_i/T -/+ span^2 alpha(T);
+ *   tau_U = k-th smallest UCB over non-eliminated points, tau_L = min((k+1)-th
+ *   smallest LCB over them, smallest LCB of an eliminated point);
+ *   eliminates i if LCB_i > tau_U, accepts i if UCB_i < tau_L;
+ *   stops when active+accepted <= k+h, accepted >= k, or after an exact round.
+ *   Output: accepted points by (estimate, index), then active points by
+ *   (estimate, index), at most k+h.
+ *
+ * X:        n x m float32 (device).           Q: nq x m float32 (device).
+ * delta:    in (0,1); FOOTNOTE additionally needs delta/n < 1/e.
+ * out_idx:  nq x (k+h) int64, -1 padded (device, required).
+ * out_count:nq int32 candidates returned (device, required).
+ * out_evals:nq int64 coordinate evaluations: samples drawn + m per exact
+ *           distance (device, required).
+ * out_rounds: nq int32 rounds run (device, may be NULL).
+ * log_code: nq x n int32 decision log, 4*round + kind (kind 0 still active at
+ *           the end, 1 eliminated, 2 accepted) (device, may be NULL).
+ * log_S:    nq x n float32 sum S_i at the point's decision (device, may be NULL;
+ *           only written when log_code is given).
+ * Non-finite data give out_count = 0 for the affected queries.
+ */
+knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                        int32_t k, double delta, uint64_t seed, const knn_opts* opts,
+                        int64_t* out_idx, int32_t* out_count, int64_t* out_evals,
+                        int32_t* out_rounds, int32_t* log_code, float* log_S,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * knn_rerank -- exact distances of candidate points, then top-k.
+ *
+ * For each query q, computes d = sum_j (X[c,j] - Q[q,j])^2 in FP64 for each
+ * candidate c = cand[q, t] (t < ncand; entries < 0 are skipped) and returns
+ * the k smallest by (d, index) (Section 3's brute force restricted to the
+ * candidates; the last step of returning the k nearest from the set S-hat).
+ * out_idx: nq x k int64 (-1 padded when fewer valid candidates);
+ * out_dist: nq x k float64 squared distances (+inf padded).
+ * ncand <= 4096. No workspace.
+ */
+knn_status knn_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                      const int64_t* cand, int32_t ncand, int32_t k,
+                      int64_t* out_idx, double* out_dist, void* stream);
+
+/*
+ * knn_exact -- the naive exact method (Section 3: all distances, then
+ * select): a screening pass computes ||x_i||^2 - 2 x_i.q + ||q||^2 for every
+ * pair, keeps every point whose screened value is within the screen's
+ * proven rounding bound of the k-th smallest, and knn_rerank's FP64 step
+ * picks the exact k nearest among them.
+ * out_idx: nq x k int64; out_dist: nq x k float64.
+ */
+size_t knn_exact_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k);
+knn_status knn_exact(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
+                     int64_t* out_idx, double* out_dist,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* knn_last_error(void);
+
+/* Library version string. */
+const char* knn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

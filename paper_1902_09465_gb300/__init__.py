@@ -7,14 +7,12 @@ The compute path is a C-ABI CUDA library (``csrc/``, built for sm_103a);
 generators.
 """
 
-__all__ = ["knn", "synth"]
+import importlib
+
+__all__ = ["knn", "synth", "build"]
 
 
 def __getattr__(name):
-    if name == "knn":
-        from . import knn as _knn
-        return _knn
-    if name == "synth":
-        from . import synth as _synth
-        return _synth
+    if name in __all__:
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,82 @@
+// api.cu -- host runtime of the C ABI: error messages, device queries and
+// stream-ordered workspaces.
+#include <mutex>
+#include <string>
+
+#include "knn_internal.h"
+
+namespace knn {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+knn_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return KNN_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return KNN_ECUDA;
+}
+
+knn_status device_info(DeviceInfo* di) {
+  static std::mutex mu;
+  static DeviceInfo cache[64];
+  static bool have[64] = {};
+  int dev = 0;
+  knn_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (s != KNN_OK) return s;
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range");
+    return KNN_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!have[dev]) {
+    DeviceInfo d;
+    d.device = dev;
+    s = cuda_check(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+    if (s == KNN_OK) s = cuda_check(cudaDeviceGetAttribute(&d.major, cudaDevAttrComputeCapabilityMajor, dev), "cc");
+    if (s == KNN_OK) s = cuda_check(cudaDeviceGetAttribute(&d.minor, cudaDevAttrComputeCapabilityMinor, dev), "cc");
+    int optin = 0;
+    if (s == KNN_OK)
+      s = cuda_check(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem optin");
+    if (s != KNN_OK) return s;
+    d.smem_optin = (size_t)optin;
+    cache[dev] = d;
+    have[dev] = true;
+  }
+  *di = cache[dev];
+  return KNN_OK;
+}
+
+knn_status Workspace::acquire(void* user, size_t user_bytes, size_t need, cudaStream_t s) {
+  stream = s;
+  if (user) {
+    if (user_bytes < need) {
+      set_error("workspace too small: need " + std::to_string(need) + " bytes, got " + std::to_string(user_bytes));
+      return KNN_ENOMEM;
+    }
+    ptr = user;
+    owned = false;
+    return KNN_OK;
+  }
+  cudaError_t e = cudaMallocAsync(&ptr, need, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaMallocAsync(workspace): ") + cudaGetErrorString(e));
+    ptr = nullptr;
+    return KNN_ENOMEM;
+  }
+  owned = true;
+  return KNN_OK;
+}
+
+void Workspace::release() {
+  if (owned && ptr) cudaFreeAsync(ptr, stream);
+  ptr = nullptr;
+  owned = false;
+}
+
+}  // namespace knn
+
+extern "C" const char* knn_last_error(void) { return knn::g_last_error.c_str(); }
+
+extern "C" const char* knn_version(void) { return "knn_gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,250 @@
+// exact.cu -- the naive exact k-NN method the paper compares against
+// (Section 3: compute all distances, then select), as
+//   screen   D~[q,i] = ||x_i||^2 + ||q||^2 - 2 x_i.q  (a GEMM, FP32 here)
+//   select   per query, the k-th smallest screened value tau~ and every
+//            point with D~ <= tau~ + 2E_q, E_q a proven bound on the screen's
+//            rounding error for that query
+//   rerank   exact FP64 distances of those candidates, top-k by (d, index).
+// The candidate rule is exact: k points have D~ <= tau~, so the k-th true
+// distance is at most tau~ + E_q, and every true k-nearest point j has
+// D~_j <= d_j + E_q <= tau~ + 2 E_q.
+#include <cfloat>
+#include <cmath>
+
+#include "knn_common.cuh"
+#include "knn_internal.h"
+
+namespace knn {
+
+knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
+                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream);
+
+constexpr int kExactCand = 2048;  // candidate slots per query before falling back to a full scan
+
+// Squared norms of rows (FP32, one warp per row) and the largest of them.
+__global__ void row_norms_kernel(const float* __restrict__ A, int64_t rows, int m, float* __restrict__ out,
+                                 unsigned* max_bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned mx = 0;
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += warps) {
+    const float* ar = A + (size_t)r * m;
+    float s = 0.0f;
+    for (int j = lane; j < m; j += 32) {
+      const float v = __ldg(ar + j);
+      s = fmaf(v, v, s);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      out[r] = s;
+      mx = max(mx, __float_as_uint(s));
+    }
+  }
+  if (lane == 0 && max_bits) atomicMax(max_bits, mx);
+}
+
+// FP32 SIMT screen: D[q*n + i] = xn[i] + qn[q] - 2 sum_j X[i,j] Q[q,j].
+// 128 x 128 tile (points x queries), k-step 8, 256 threads with 8 x 8
+// outputs each, double-buffered shared memory.
+constexpr int kBM = 128, kBN = 128, kBK = 8;
+
+__global__ void __launch_bounds__(256) screen_sgemm_kernel(const float* __restrict__ X, const float* __restrict__ Q,
+                                                           int64_t n, int nq, int m, const float* __restrict__ xn,
+                                                           const float* __restrict__ qn, float* __restrict__ D) {
+  __shared__ __align__(16) float As[2][kBK][kBM];
+  __shared__ __align__(16) float Bs[2][kBK][kBN];
+  const int tid = threadIdx.x;
+  const int64_t p0 = (int64_t)blockIdx.x * kBM;
+  const int q0 = blockIdx.y * kBN;
+  // loader: each thread brings 4 consecutive k of one row of each operand
+  const int lrow = tid >> 1, lk = (tid & 1) * 4;
+  const int64_t arow = p0 + lrow;
+  const int brow = q0 + lrow;
+  const bool aok = arow < n, bok = brow < nq;
+  const float* ap = X + (size_t)(aok ? arow : 0) * m;
+  const float* bp = Q + (size_t)(bok ? brow : 0) * m;
+  const int tp = tid & 15, tq = tid >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+
+  auto load = [&](int kb, float ra[4], float rb[4]) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int kk = kb + lk + e;
+      ra[e] = (aok && kk < m) ? __ldg(ap + kk) : 0.0f;
+      rb[e] = (bok && kk < m) ? __ldg(bp + kk) : 0.0f;
+    }
+  };
+  float ra[4], rb[4];
+  load(0, ra, rb);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    As[0][lk + e][lrow] = ra[e];
+    Bs[0][lk + e][lrow] = rb[e];
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int kb = 0; kb < m; kb += kBK) {
+    const bool more = kb + kBK < m;
+    if (more) load(kb + kBK, ra, rb);
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tp * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tp * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tq * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tq * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    if (more) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        As[buf ^ 1][lk + e][lrow] = ra[e];
+        Bs[buf ^ 1][lk + e][lrow] = rb[e];
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+  // epilogue: point i = p0 + {tp*4 + e, 64 + tp*4 + e}, query q = q0 + {tq*4 + e, 64 + tq*4 + e}
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int q = q0 + (j < 4 ? tq * 4 + j : 64 + tq * 4 + (j - 4));
+    if (q >= nq) continue;
+    const float qv = qn[q];
+    float* drow = D + (size_t)q * n;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t p = p0 + (i < 4 ? tp * 4 + i : 64 + tp * 4 + (i - 4));
+      if (p < n) drow[p] = (xn[p] + qv) - 2.0f * acc[i][j];
+    }
+  }
+}
+
+// Per query: k-th smallest screened value, then every point within 2 E_q of
+// it into cand[q, 0..kExactCand) (-1 padded); a row that does not fit is
+// marked -2 (rerank then scans every point).
+constexpr int kSelNT = 512;
+
+__global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __restrict__ D, int64_t n, int m, int k,
+                                                               const float* __restrict__ qn,
+                                                               const unsigned* __restrict__ xn_max_bits,
+                                                               int64_t* __restrict__ cand) {
+  __shared__ uint32_t hist[kHistBins];
+  __shared__ uint32_t buf[kSelCap];
+  __shared__ BlockScratch<kSelNT> bs;
+  __shared__ SelectShared ss;
+  __shared__ int cnt;
+  const int q = blockIdx.x;
+  const float* dr = D + (size_t)q * n;
+  for (int i = threadIdx.x; i < kHistBins; i += kSelNT) hist[i] = 0;
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += kSelNT) atomicAdd(&hist[f2key(__ldg(dr + i)) >> 20], 1u);
+  __syncthreads();
+  select_smallest<kSelNT>([&](int i) { return f2key(__ldg(dr + i)); }, (int)n, k, hist, buf, ss, bs);
+  const float tau = key2f(buf[k - 1]);
+  // Rounding bound of the screen (unit roundoff u = 2^-24): the dot product
+  // and the two norms are length-m FP32 sums (error <= gamma_m times the
+  // sum of magnitudes, gamma_m = m u / (1 - m u)), plus two final roundings;
+  // all magnitudes are bounded by (||x|| + ||q||)^2. The norms themselves
+  // carry relative error gamma_m; a factor 2 covers the second-order terms.
+  const double u = 1.0 / 16777216.0;
+  const double gm = (double)(m + 2) * u / (1.0 - (double)(m + 2) * u);
+  const double xmax = sqrt((double)__uint_as_float(*xn_max_bits) * (1.0 + gm));
+  const double qq = sqrt((double)qn[q] * (1.0 + gm));
+  const double E = 2.0 * (gm + 4.0 * u) * (xmax + qq) * (xmax + qq);
+  const float thr = (float)((double)tau + 2.0 * E) * (1.0f + 4.0f / 16777216.0f);
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int64_t* cr = cand + (size_t)q * kExactCand;
+  for (int64_t i = threadIdx.x; i < n; i += kSelNT) {
+    if (__ldg(dr + i) <= thr) {
+      const int p = atomicAdd(&cnt, 1);
+      if (p < kExactCand) cr[p] = i;
+    }
+  }
+  __syncthreads();
+  const int c = cnt;
+  if (c > kExactCand) {
+    for (int t = threadIdx.x; t < kExactCand; t += kSelNT) cr[t] = t == 0 ? -2 : -1;
+  } else {
+    for (int t = c + threadIdx.x; t < kExactCand; t += kSelNT) cr[t] = -1;
+  }
+}
+
+struct ExactCarve {
+  float* xn;
+  float* qn;
+  unsigned* xmax;
+  float* D;
+  int64_t* cand;
+};
+
+static size_t carve_exact(Carve& cv, int64_t n, int32_t nq, ExactCarve* out) {
+  ExactCarve c;
+  c.xn = cv.take<float>((size_t)n);
+  c.qn = cv.take<float>((size_t)nq);
+  c.xmax = cv.take<unsigned>(1);
+  c.D = cv.take<float>((size_t)nq * (size_t)n);
+  c.cand = cv.take<int64_t>((size_t)nq * kExactCand);
+  if (out) *out = c;
+  return cv.off;
+}
+
+}  // namespace knn
+
+using namespace knn;
+
+extern "C" size_t knn_exact_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k) {
+  (void)m;
+  (void)k;
+  Carve cv;
+  return carve_exact(cv, n, nq, nullptr) + 256;
+}
+
+extern "C" knn_status knn_exact(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
+                                int64_t* out_idx, double* out_dist, void* workspace, size_t workspace_bytes,
+                                void* stream_) {
+  clear_error();
+  if (n < 1 || n >= (int64_t)1 << 31 || m < 1 || m > kMaxM || nq < 0 || k < 1 || k > n || k > kMaxKH) {
+    set_error("knn_exact: need 1 <= n < 2^31, 1 <= m <= 16384, 1 <= k <= min(n, 1024)");
+    return KNN_EINVAL;
+  }
+  if (nq == 0) return KNN_OK;
+  if (!X || !Q || !out_idx || !out_dist) {
+    set_error("knn_exact: null pointer");
+    return KNN_EINVAL;
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  Carve measure;
+  const size_t need = carve_exact(measure, n, nq, nullptr) + 256;
+  Workspace ws;
+  knn_status s = ws.acquire(workspace, workspace_bytes, need, stream);
+  if (s != KNN_OK) return s;
+  Carve cv;
+  cv.base = reinterpret_cast<uint8_t*>(((uintptr_t)ws.ptr + 255) & ~uintptr_t(255));
+  ExactCarve c;
+  carve_exact(cv, n, nq, &c);
+  DeviceInfo di;
+  device_info(&di);
+  s = cuda_check(cudaMemsetAsync(c.xmax, 0, 4, stream), "memset");
+  if (s == KNN_OK) {
+    row_norms_kernel<<<di.sms * 8, 256, 0, stream>>>(X, n, m, c.xn, c.xmax);
+    row_norms_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(Q, nq, m, c.qn, nullptr);
+    dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((nq + kBN - 1) / kBN));
+    screen_sgemm_kernel<<<grid, 256, 0, stream>>>(X, Q, n, nq, m, c.xn, c.qn, c.D);
+    screen_select_kernel<<<nq, kSelNT, 0, stream>>>(c.D, n, m, k, c.qn, c.xmax, c.cand);
+    s = cuda_check(cudaGetLastError(), "exact kernels launch");
+  }
+  if (s == KNN_OK) s = launch_rerank(X, n, m, Q, nq, c.cand, kExactCand, k, out_idx, out_dist, stream);
+  ws.release();
+  return s;
+}

@@ -1,0 +1,53 @@
+// knn_internal.h -- host-side helpers shared by the library's translation
+// units: error reporting, workspace carving and device queries.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/knn_gb300.h"
+
+namespace knn {
+
+void set_error(const std::string& msg);
+void clear_error();
+
+// Returns KNN_ECUDA and records the message if `e` is an error.
+knn_status cuda_check(cudaError_t e, const char* what);
+
+// Bump allocator over a caller-provided device buffer (256-byte aligned
+// pieces). With base == nullptr it only measures.
+struct Carve {
+  uint8_t* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct DeviceInfo {
+  int device = 0;
+  int sms = 0;
+  int major = 0, minor = 0;
+  size_t smem_optin = 0;
+};
+knn_status device_info(DeviceInfo* di);
+
+// Stream-ordered workspace: either the caller's buffer or an allocation
+// released on the same stream by release().
+struct Workspace {
+  void* ptr = nullptr;
+  bool owned = false;
+  cudaStream_t stream = nullptr;
+  knn_status acquire(void* user, size_t user_bytes, size_t need, cudaStream_t s);
+  void release();
+};
+
+}  // namespace knn

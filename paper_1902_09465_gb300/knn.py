@@ -1,0 +1,176 @@
+"""Thin Python binding of ``libknn_gb300.so`` (C ABI in include/knn_gb300.h).
+
+Argument marshalling only: tensors are checked for device, dtype and layout,
+outputs are allocated with torch on the inputs' device, and the library's
+entry points are called with raw device pointers on the current torch
+stream. Every step of the computation runs in the library's CUDA kernels.
+There is no CPU fallback: without the built library every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libknn_gb300.so")
+_lock = threading.Lock()
+_lib = None
+
+BOUNDS = {"footnote": 0, "lemma": 1, "exp": 2}
+ACTIVE, ELIMINATED, ACCEPTED = 0, 1, 2
+FULL_MASK = (1 << 64) - 1
+
+
+class KnnError(RuntimeError):
+    pass
+
+
+class Opts(C.Structure):
+    _fields_ = [("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double), ("B0", C.c_int32),
+                ("B", C.c_int32), ("grow", C.c_int32), ("qid_base", C.c_uint64), ("mask_p", C.c_uint64),
+                ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "knn_opts_default": (None, [C.POINTER(Opts)]),
+    "knn_adaptive_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.POINTER(Opts)]),
+    "knn_adaptive": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
+                               C.POINTER(Opts), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "knn_rerank": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P]),
+    "knn_exact_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, C.c_int32, C.c_int32]),
+    "knn_exact": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
+    "knn_last_error": (C.c_char_p, []),
+    "knn_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise KnnError(f"{LIB_PATH} is missing: build it with paper_1902_09465_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        msg = lib().knn_last_error().decode()
+        raise KnnError(f"knn status {rc}: {msg}")
+
+
+def _dev(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise KnnError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise KnnError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise KnnError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid_base=0, share_points=False,
+              share_queries=False, max_ctas=0) -> Opts:
+    o = Opts()
+    lib().knn_opts_default(C.byref(o))
+    o.h = -1 if h is None else int(h)
+    o.bound = BOUNDS[bound] if isinstance(bound, str) else int(bound)
+    o.c_alpha = float(c_alpha)
+    o.B0, o.B, o.grow = int(B0), int(B), int(grow)
+    o.qid_base = int(qid_base)
+    o.mask_p = 0 if share_points else FULL_MASK
+    o.mask_q = 0 if share_queries else FULL_MASK
+    o.max_ctas = int(max_ctas)
+    return o
+
+
+def adaptive_workspace_size(n, m, nq, k, opts: Opts) -> int:
+    return int(lib().knn_adaptive_workspace_size(int(n), int(m), int(nq), int(k), C.byref(opts)))
+
+
+def adaptive(X: torch.Tensor, Q: torch.Tensor, k: int, delta: float = 0.01, seed: int = 0, *, trace: bool = False,
+             workspace: torch.Tensor | None = None, stream=None, out=None, **opt_kw):
+    """Batched adaptive rounds for every row of Q against X (knn_adaptive).
+
+    Returns a dict: idx [nq, k+h] int64 (-1 padded), count [nq] int32,
+    evals [nq] int64, rounds [nq] int32 and, with trace=True, code [nq, n]
+    int32 (4*round + kind) and S [nq, n] float32.
+    """
+    n, m = X.shape
+    nq = Q.shape[0]
+    if Q.shape[1] != m:
+        raise KnnError("X and Q must have the same number of columns")
+    o = make_opts(k, **opt_kw)
+    h = k if o.h < 0 else o.h
+    dev = X.device
+    if out is None:
+        out = {"idx": torch.empty((nq, k + h), dtype=torch.int64, device=dev),
+               "count": torch.empty(nq, dtype=torch.int32, device=dev),
+               "evals": torch.empty(nq, dtype=torch.int64, device=dev),
+               "rounds": torch.empty(nq, dtype=torch.int32, device=dev)}
+    if trace:
+        out["code"] = torch.empty((nq, n), dtype=torch.int32, device=dev)
+        out["S"] = torch.empty((nq, n), dtype=torch.float32, device=dev)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = _dev(workspace, "workspace", torch.uint8), workspace.numel()
+    rc = lib().knn_adaptive(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, int(k), float(delta), int(seed), C.byref(o),
+                            _dev(out["idx"], "idx", torch.int64), _dev(out["count"], "count", torch.int32),
+                            _dev(out["evals"], "evals", torch.int64), _dev(out["rounds"], "rounds", torch.int32),
+                            _dev(out["code"], "code", torch.int32) if trace else None,
+                            _dev(out["S"], "S") if trace else None, ws_ptr, ws_bytes, _stream(stream))
+    _check(rc)
+    return out
+
+
+def rerank(X: torch.Tensor, Q: torch.Tensor, cand: torch.Tensor, k: int, stream=None):
+    """Exact FP64 distances of the candidates of each query, top-k by
+    (distance, index) (knn_rerank). Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+    n, m = X.shape
+    nq, ncand = cand.shape
+    idx = torch.empty((nq, k), dtype=torch.int64, device=X.device)
+    dist = torch.empty((nq, k), dtype=torch.float64, device=X.device)
+    rc = lib().knn_rerank(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, _dev(cand, "cand", torch.int64), ncand, int(k),
+                          _dev(idx, "idx", torch.int64), _dev(dist, "dist", torch.float64), _stream(stream))
+    _check(rc)
+    return idx, dist
+
+
+def exact_workspace_size(n, m, nq, k) -> int:
+    return int(lib().knn_exact_workspace_size(int(n), int(m), int(nq), int(k)))
+
+
+def exact(X: torch.Tensor, Q: torch.Tensor, k: int, workspace: torch.Tensor | None = None, stream=None):
+    """Naive exact k-NN (knn_exact). Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+    n, m = X.shape
+    nq = Q.shape[0]
+    idx = torch.empty((nq, k), dtype=torch.int64, device=X.device)
+    dist = torch.empty((nq, k), dtype=torch.float64, device=X.device)
+    ws_ptr, ws_bytes = None, 0
+    if workspace is not None:
+        ws_ptr, ws_bytes = _dev(workspace, "workspace", torch.uint8), workspace.numel()
+    rc = lib().knn_exact(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, int(k), _dev(idx, "idx", torch.int64),
+                         _dev(dist, "dist", torch.float64), ws_ptr, ws_bytes, _stream(stream))
+    _check(rc)
+    return idx, dist
+
+
+def version() -> str:
+    return lib().knn_version().decode()

@@ -1,0 +1,74 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+that include/*.h declares (no compute calls: these run without a GPU)."""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1902_09465_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for mt in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(knn_\w+)\s*\(", text, flags=re.M):
+            names.add(mt.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("knn_adaptive", "knn_exact", "knn_rerank", "knn_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    L = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_version_and_defaults_without_gpu(lib_path):
+    from paper_1902_09465_gb300 import knn
+    assert "sm_103a" in knn.version()
+    o = knn.Opts()
+    knn.lib().knn_opts_default(ctypes.byref(o))
+    assert o.h == -1 and o.B0 >= 1 and o.B >= 1 and o.mask_p == (1 << 64) - 1
+
+
+def test_invalid_arguments_are_rejected_on_the_host(lib_path):
+    from paper_1902_09465_gb300 import knn
+    L = knn.lib()
+    o = knn.Opts()
+    L.knn_opts_default(ctypes.byref(o))
+    # k > n, delta outside (0,1), m = 0: all refused before any device work
+    for (n, m, k, delta) in [(10, 4, 11, 0.1), (10, 4, 2, 1.5), (10, 0, 2, 0.1), (10, 4, 2, 0.0)]:
+        rc = L.knn_adaptive(None, n, m, None, 1, k, delta, 0, ctypes.byref(o), None, None, None, None, None,
+                            None, None, 0, None)
+        assert rc == 1
+        assert L.knn_last_error().decode()
+    rc = L.knn_rerank(None, 10, 4, None, 1, None, 0, 1, None, None, None)
+    assert rc == 1
+
+
+def test_oracle_and_library_share_no_code():
+    lib_src = glob.glob(os.path.join(ROOT, "paper_1902_09465_gb300", "**", "*"), recursive=True)
+    for f in lib_src:
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            text = open(f).read()
+            assert "knn_oracle" not in text and "import oracle" not in text and "from oracle" not in text, f
+    for f in glob.glob(os.path.join(ROOT, "oracle", "*")):
+        if f.endswith((".py", ".c", ".h")):
+            text = open(f).read()
+            assert "knn_gb300" not in text and "paper_1902_09465_gb300" not in text, f
