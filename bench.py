@@ -368,7 +368,11 @@ def main():
     ap.add_argument("--B", type=int, default=16)
     ap.add_argument("--grow", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nq", type=int, default=None, help="queries per GPU (default 1024)")
     args = ap.parse_args()
+    if args.nq:
+        WORKLOAD["nq"] = args.nq
+        WORKLOAD["name"] = WORKLOAD["name"].replace("nq=1024", f"nq={args.nq}")
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
     rank = int(os.environ.get("RANK", "0"))

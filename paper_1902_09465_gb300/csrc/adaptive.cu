@@ -280,6 +280,8 @@ __global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) 
     qmin = block_min<NT>(qmin, sh.bs);
     qmax = block_max<NT>(qmax, sh.bs);
     const float xmin = key2f(a.xrange[0]), xmax = key2f(a.xrange[1]);
+    // fminf/fmaxf drop NaN operands, so the data range is tested on its own
+    bad |= !(isfinite(xmin) && isfinite(xmax));
     const float span = fmaxf(xmax, qmax) - fminf(xmin, qmin);
     const float span2 = span * span;
     if (bad || !isfinite(span2)) {

@@ -107,3 +107,17 @@ def test_containment_binary_data_gpu():
         ti, _ = oracle.exact_knn(X, q, 3)
         fails += not set(ti[0]) <= set(g["idx"][0][: g["count"][0]])
     assert fails <= stats.binom.ppf(0.999, trials, 0.05)
+
+
+def test_full_size_pixel_workload_sampled_queries():
+    """The benchmark workload at full size (n=100,000, d=784, 1,024 queries,
+    k=10) in the benchmark's launch configuration; three queries replayed."""
+    import bench
+    X, Q, _ = bench.make_inputs(0)
+    summ, gpu = check(X, Q, 10, delta=0.01, seed=0, queries=[0, 511, 1023], bound="exp", c_alpha=1e-3,
+                      B0=16, B=16, grow=1)
+    assert summ["queries"] == 3
+    assert np.all(gpu["count"] <= 20) and np.all(gpu["count"] >= 10)
+    ti, _ = oracle.exact_knn(X, Q[[0, 511, 1023]], 10)
+    for j, q in enumerate([0, 511, 1023]):
+        assert set(ti[j]) <= set(gpu["idx"][q][: gpu["count"][q]])
