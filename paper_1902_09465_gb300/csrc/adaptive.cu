@@ -40,7 +40,7 @@ struct AdaptiveArgs {
   float a_c0, a_c1, c_alpha;  // host-precomputed constants of alpha(u)
   int32_t B0, B, grow;
   uint64_t seed, qid_base, mask_p, mask_q;
-  const uint32_t* xrange;  // ordered keys of min(X), max(X)
+  const uint32_t* xrange;  // ordered keys of min(X), max(X) over finite values; [2] non-finite flag
   int32_t* ws_ids;
   float* ws_S;
   float* ws_C;
@@ -280,8 +280,7 @@ __global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) 
     qmin = block_min<NT>(qmin, sh.bs);
     qmax = block_max<NT>(qmax, sh.bs);
     const float xmin = key2f(a.xrange[0]), xmax = key2f(a.xrange[1]);
-    // fminf/fmaxf drop NaN operands, so the data range is tested on its own
-    bad |= !(isfinite(xmin) && isfinite(xmax));
+    bad |= a.xrange[2] != 0u;  // non-finite data (flagged by the range pass)
     const float span = fmaxf(xmax, qmax) - fminf(xmin, qmin);
     const float span2 = span * span;
     if (bad || !isfinite(span2)) {
@@ -513,24 +512,31 @@ __global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) 
   }
 }
 
-// Range of the data as ordered keys: xr[0] = min, xr[1] = max (NaN sorts
-// outside +-inf, so a NaN anywhere makes the span non-finite).
+// Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and
+// xr[2] = 1 if any element is NaN or infinite.
 __global__ void minmax_kernel(const float* __restrict__ X, size_t count, uint32_t* xr) {
-  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u, bad = 0u;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    const uint32_t key = f2key(__ldg(X + i));
-    lo = min(lo, key);
-    hi = max(hi, key);
+    const float v = __ldg(X + i);
+    if (isfinite(v)) {
+      const uint32_t key = f2key(v);
+      lo = min(lo, key);
+      hi = max(hi, key);
+    } else {
+      bad = 1u;
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
     hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicMin(&xr[0], lo);
     atomicMax(&xr[1], hi);
+    if (bad) atomicOr(&xr[2], 1u);
   }
 }
 
@@ -592,7 +598,7 @@ struct AdaptiveCarve {
 
 static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, AdaptiveCarve* out) {
   AdaptiveCarve c;
-  c.xrange = cv.take<uint32_t>(2);
+  c.xrange = cv.take<uint32_t>(3);
   c.queue = cv.take<int32_t>(1);
   const size_t per = (size_t)p.grid * 2 * (size_t)n;
   c.ids = cv.take<int32_t>(per);
@@ -691,7 +697,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
 
   // span: min/max of the data (keys), then the rounds
   s = cuda_check(cudaMemsetAsync(c.xrange, 0xFF, 4, stream), "memset(range)");
-  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(c.xrange + 1, 0x00, 4, stream), "memset(range)");
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(c.xrange + 1, 0x00, 8, stream), "memset(range)");
   if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
   if (s != KNN_OK) {
     ws.release();
