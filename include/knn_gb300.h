@@ -109,6 +109,37 @@ knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const float* Q, in
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * knn_adaptive_noalloc -- knn_adaptive for callers that cannot allocate device
+ * memory. (The paper has no counterpart: this is a deployment variant.)
+ *
+ * Some callers cannot call cudaMalloc: code running inside a host framework
+ * that has already reserved all device memory in its own pool, plugins whose
+ * host forbids outside allocations, or latency-critical paths that must not
+ * risk an allocation failing or stalling. This entry point allocates nothing:
+ * it runs the same round-loop kernel as knn_adaptive, with the same
+ * arguments and outputs (all caller-owned), and takes its scratch from a
+ * fixed array of knn_adaptive_noalloc_scratch_bytes() bytes (64 MiB) that
+ * every GPU which loads the library holds until the process exits.
+ *
+ * - The scratch needs about 24 n bytes per query processed at a time; the
+ *   call runs as many queries at once as fit (fewer than knn_adaptive when n
+ *   is large) and returns KNN_EINVAL with a message when even one query's
+ *   lists exceed the array (n above roughly 2.7 million).
+ * - The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ * - Every call shares the one array and starts by resetting the parts that
+ *   must start fresh. Calls whose work overlaps on the GPU (on different
+ *   streams or from different threads without ordering) race on the array
+ *   and give wrong results; order them on one stream.
+ */
+size_t knn_adaptive_noalloc_scratch_bytes(void);
+knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                                int32_t k, double delta, uint64_t seed, const knn_opts* opts,
+                                int64_t* out_idx, int32_t* out_count, int64_t* out_evals,
+                                int32_t* out_rounds, int32_t* log_code, float* log_S, void* stream);
+
+/*
  * knn_rerank -- exact distances of candidate points, then top-k.
  *
  * For each query q, computes d = sum_j (X[c,j] - Q[q,j])^2 in FP64 for each

@@ -22,6 +22,8 @@
 // per-round scalar, and the per-point state is (id, S, Kahan term).
 #include <cfloat>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "knn_common.cuh"
@@ -764,4 +766,146 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   s = cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
   ws.release();
   return s;
+}
+
+// ------------------------------------------------- entry without allocation
+// knn_adaptive_noalloc runs the same round-loop kernel as knn_adaptive but
+// takes its scratch (data range, work-queue counter, the per-CTA active lists
+// and accepted lists) from this fixed array instead of a workspace. Every GPU
+// that loads the library holds the array until the process exits.
+namespace knn {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64] = {};  // device address of the array, per device
+
+// In host code the array's name is only a host-side stand-in; the device
+// address is looked up once per device, with that device current.
+static knn_status noalloc_address(void** out) {
+  int dev = 0;
+  knn_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (s != KNN_OK) return s;
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range");
+    return KNN_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    s = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(no-alloc scratch)");
+    if (s != KNN_OK) return s;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return KNN_OK;
+}
+
+}  // namespace knn
+
+extern "C" size_t knn_adaptive_noalloc_scratch_bytes(void) { return knn::kNoAllocScratchBytes; }
+
+extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                                           int32_t k, double delta, uint64_t seed, const knn_opts* opts,
+                                           int64_t* out_idx, int32_t* out_count, int64_t* out_evals,
+                                           int32_t* out_rounds, int32_t* log_code, float* log_S, void* stream_) {
+  clear_error();
+  const knn_opts o = resolve(opts, k);
+  knn_status s = validate(n, m, nq, k, delta, o);
+  if (s != KNN_OK) return s;
+  if (o.threads != 0 && o.threads != kAdaptiveNT) {
+    set_error("threads must be 0 or 512");
+    return KNN_EINVAL;
+  }
+  if (nq == 0) return KNN_OK;
+  if (!X || !Q || !out_idx || !out_count || !out_evals) {
+    set_error("X, Q, out_idx, out_count and out_evals are required");
+    return KNN_EINVAL;
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  AdaptivePlan p;
+  s = plan_adaptive(n, m, nq, k, &o, &p);
+  if (s != KNN_OK) return s;
+  // as many resident CTAs as the fixed scratch holds (each needs 24 n bytes)
+  for (;;) {
+    Carve measure;
+    if (carve_adaptive(measure, n, p, nullptr) <= kNoAllocScratchBytes) break;
+    if (p.grid == 1) {
+      Carve one;
+      set_error("knn_adaptive_noalloc: n = " + std::to_string(n) + " needs " +
+                std::to_string(carve_adaptive(one, n, p, nullptr)) + " bytes of scratch for one query at a time; " +
+                "the fixed scratch is " + std::to_string(kNoAllocScratchBytes) + " bytes");
+      return KNN_EINVAL;
+    }
+    p.grid = p.grid > 8 ? p.grid - p.grid / 8 : p.grid - 1;
+  }
+  void* base = nullptr;
+  s = noalloc_address(&base);
+  if (s != KNN_OK) return s;
+  Carve cv;
+  cv.base = static_cast<uint8_t*>(base);  // the array is 256-byte aligned
+  AdaptiveCarve c;
+  carve_adaptive(cv, n, p, &c);
+
+  // the array keeps the previous call's contents: reset what must start fresh
+  s = cuda_check(cudaMemsetAsync(c.xrange, 0xFF, 4, stream), "memset(range)");
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(c.xrange + 1, 0x00, 8, stream), "memset(range)");
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
+  if (s != KNN_OK) return s;
+  {
+    DeviceInfo di;
+    device_info(&di);
+    const size_t count = (size_t)n * (size_t)m;
+    int blocks = (int)std::min<size_t>((count + 255) / 256, (size_t)di.sms * 8);
+    if (blocks < 1) blocks = 1;
+    minmax_kernel<<<blocks, 256, 0, stream>>>(X, count, c.xrange);
+    s = cuda_check(cudaGetLastError(), "minmax_kernel launch");
+    if (s != KNN_OK) return s;
+  }
+  AdaptiveArgs a;
+  a.X = X;
+  a.Q = Q;
+  a.n = n;
+  a.m = m;
+  a.nq = nq;
+  a.k = k;
+  a.h = o.h;
+  a.bound = o.bound;
+  const double dprime = delta / (double)n;
+  a.a_c0 = 0.0f;
+  a.a_c1 = 0.0f;
+  if (o.bound == KNN_BOUND_FOOTNOTE)
+    a.a_c0 = (float)(std::log(1.0 / dprime) + 3.0 * std::log(std::log(1.0 / dprime)));
+  else if (o.bound == KNN_BOUND_LEMMA)
+    a.a_c0 = (float)std::log(125.0 / dprime);
+  else
+    a.a_c1 = (float)((double)n / delta);
+  a.c_alpha = (float)o.c_alpha;
+  a.B0 = o.B0;
+  a.B = o.B;
+  a.grow = o.grow;
+  a.seed = seed;
+  a.qid_base = o.qid_base;
+  a.mask_p = o.mask_p;
+  a.mask_q = o.mask_q;
+  a.xrange = c.xrange;
+  a.ws_ids = c.ids;
+  a.ws_S = c.S;
+  a.ws_C = c.C;
+  a.ws_acc_id = c.acc_id;
+  a.ws_acc_d = c.acc_d;
+  a.ws_acc_U = c.acc_U;
+  a.ws_acc_L = c.acc_L;
+  a.acc_cap = p.acc_cap;
+  a.queue = c.queue;
+  a.out_idx = out_idx;
+  a.out_count = out_count;
+  a.out_evals = out_evals;
+  a.out_rounds = out_rounds;
+  a.log_code = log_code;
+  a.log_S = log_code ? log_S : nullptr;
+  a.vec4 = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  adaptive_rounds_kernel<kAdaptiveNT><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
+  return cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
 }
