@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 BOUND = {"footnote": 0, "lemma": 1, "exp": 2}
+STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
 ACTIVE, ELIMINATED, ACCEPTED = 0, 1, 2
 
 
@@ -43,7 +44,7 @@ class AdaptiveParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double),
                 ("delta", C.c_double), ("B0", C.c_int32), ("B", C.c_int32), ("grow", C.c_int32),
                 ("seed", C.c_uint64), ("qid", C.c_uint64), ("mask_p", C.c_uint64), ("mask_q", C.c_uint64),
-                ("tol", C.c_double)]
+                ("tol", C.c_double), ("storage", C.c_int32)]
 
 
 class AdaptiveStats(C.Structure):
@@ -75,6 +76,12 @@ def lib():
                                          P, P, P]
             L.orc_sequential.restype = C.c_int32
             L.orc_max_threads.restype = C.c_int32
+            L.orc_quantize.argtypes = [C.c_int32, P, C.c_int64, C.c_int32, P, P]
+            L.orc_quantize.restype = C.c_double
+            L.orc_round_bf16.argtypes = [C.c_float]
+            L.orc_round_bf16.restype = C.c_float
+            L.orc_round_e4m3.argtypes = [C.c_float]
+            L.orc_round_e4m3.restype = C.c_float
             _lib = L
     return _lib
 
@@ -100,6 +107,17 @@ def alpha(form, u, n, delta, c_alpha=1.0):
                            float(delta))
 
 
+def quantize(X, storage):
+    """Dequantised copy of X for a storage format ("f32", "bf16", "fp8"),
+    the per-row FP8 scales, and the largest element error."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n, m = X.shape
+    out = np.empty_like(X)
+    scale = np.ones(n, dtype=np.float32)
+    emax = lib().orc_quantize(STORAGE[storage], _ptr(X), n, m, _ptr(out), _ptr(scale))
+    return out, scale, float(emax)
+
+
 def max_threads() -> int:
     return int(lib().orc_max_threads())
 
@@ -117,11 +135,12 @@ def exact_knn(X, Q, k, threads=0):
 
 
 def make_params(k, h=None, delta=0.01, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, seed=0,
-                qid=0, share_points=False, share_queries=False, tol=1e-5):
+                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32"):
     full = (1 << 64) - 1
     return AdaptiveParams(int(k), int(k if h is None else h), BOUND[bound] if isinstance(bound, str) else int(bound),
                           float(c_alpha), float(delta), int(B0), int(B), int(grow), int(seed), int(qid),
-                          0 if share_points else full, 0 if share_queries else full, float(tol))
+                          0 if share_points else full, 0 if share_queries else full, float(tol),
+                          STORAGE[storage] if isinstance(storage, str) else int(storage))
 
 
 def adaptive(X, Q, params: AdaptiveParams, replay=None, want_state=True, threads=0):

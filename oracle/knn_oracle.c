@@ -89,6 +89,64 @@ double orc_alpha(int32_t form, double c_alpha, int64_t u, int64_t n, double delt
     return sqrt(c_alpha * log(1.0 + (1.0 + log(uu)) * (double)n / delta) / uu);
 }
 
+/* ------------------------------------------------------------- storage */
+
+/* bfloat16: keep the top 16 bits of the float, rounding to nearest with
+ * ties to even (NaN is left as is). */
+float orc_round_bf16(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return x;
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    float y;
+    memcpy(&y, &u, 4);
+    return y;
+}
+
+/* FP8 e4m3 (the variant without infinities): 3 fraction bits, normal
+ * exponents -6..8, subnormal spacing 2^-9, largest finite 448; round to
+ * nearest, ties to even, saturating at 448. */
+float orc_round_e4m3(float x) {
+    double a = fabs((double)x);
+    if (a == 0.0 || a != a) return x;
+    int ex;
+    frexp(a, &ex);               /* a = f 2^ex, f in [0.5, 1): binade exponent ex - 1 */
+    int e = ex - 1;
+    if (e < -6) e = -6;          /* subnormal range shares the quantum of 2^-6 */
+    double quantum = ldexp(1.0, e - 3);
+    double r = rint(a / quantum) * quantum;   /* default rounding: ties to even */
+    if (r > 448.0) r = 448.0;
+    return (float)(x < 0 ? -r : r);
+}
+
+double orc_quantize(int32_t storage, const float* X, int64_t n, int32_t m, float* out, float* scale) {
+    double emax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const float* xr = X + (size_t)i * (size_t)m;
+        float* o = out + (size_t)i * (size_t)m;
+        if (storage == ORC_STORE_BF16) {
+            for (int32_t j = 0; j < m; ++j) o[j] = orc_round_bf16(xr[j]);
+        } else if (storage == ORC_STORE_FP8) {
+            float mx = 0.0f;
+            for (int32_t j = 0; j < m; ++j) if (fabsf(xr[j]) > mx) mx = fabsf(xr[j]);
+            volatile float s = mx > 0.0f ? mx / 448.0f : 1.0f;
+            if (scale) scale[i] = s;
+            for (int32_t j = 0; j < m; ++j) {
+                volatile float t = xr[j] / s;
+                float v = orc_round_e4m3(t);
+                o[j] = (float)((double)s * (double)v);
+            }
+        } else {
+            for (int32_t j = 0; j < m; ++j) o[j] = xr[j];
+        }
+        for (int32_t j = 0; j < m; ++j) {
+            double d = fabs((double)o[j] - (double)xr[j]);
+            if (d > emax) emax = d;
+        }
+    }
+    return emax;
+}
+
 /* ----------------------------------------------------------- brute force */
 
 typedef struct { double v; int64_t i; } vi_t;
@@ -173,10 +231,13 @@ static int64_t round_samples(const orc_adaptive_params* p, int32_t r, int64_t Tc
     return p->B;
 }
 
-int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
-                     const orc_adaptive_params* p, const int32_t* replay,
-                     int64_t* out_idx, int32_t* code, double* S, int32_t* T,
-                     orc_adaptive_stats* st) {
+/* One query. X is the FP32 data (it fixes the span), G the values the
+ * samples are read from (X itself, or its dequantised BF16/FP8 copy whose
+ * elements differ from X by at most emax). */
+static int32_t adaptive_core(const float* X, const float* G, double emax, int64_t n, int32_t m, const float* q,
+                             const orc_adaptive_params* p, const int32_t* replay,
+                             int64_t* out_idx, int32_t* code, double* S, int32_t* T,
+                             orc_adaptive_stats* st) {
     const int32_t k = p->k, h = p->h;
     const int64_t kh = (int64_t)k + h;
     if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->B0 < 1 || p->B < 1)
@@ -210,7 +271,14 @@ int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
         if (X[e] > hi) hi = X[e];
     }
     const double span = hi - lo;
-    const double span2 = span * span;
+    /* A stored copy moves each sample by at most
+     * |xt - x| |xt + x - 2q| <= emax (2 span + emax), so its distances lie
+     * within eps of the true ones, and its samples within [0, (span + 2 emax)^2]:
+     * the width of the bound grows accordingly, and an exact round of the
+     * copy still carries eps. */
+    const double spanw = span + 2.0 * emax;
+    const double span2 = spanw * spanw;
+    const double eps = emax * (2.0 * span + emax);
 
     unsigned char* status = (unsigned char*)malloc((size_t)n);
     double* Sx = (double*)malloc(sizeof(double) * (size_t)n);
@@ -238,7 +306,7 @@ int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
          * would reach m ("If T = m, compute the distance exactly"). */
         for (int64_t i = 0; i < n; ++i) {
             if (status[i] != ORC_ACTIVE) continue;
-            const float* xi = X + (size_t)i * (size_t)m;
+            const float* xi = G + (size_t)i * (size_t)m;
             if (exact) {
                 Sx[i] = sqdist(xi, q, m);
             } else {
@@ -251,7 +319,7 @@ int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
             Tx[i] = (int32_t)Tn;
         }
         evals += nact * (exact ? (int64_t)m : Br);
-        const double w = exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta);
+        const double w = (exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta)) + eps;
 
         /* Bounds of the non-eliminated points: current ones for active
          * points, frozen ones for accepted points. */
@@ -362,11 +430,32 @@ int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
     return 0;
 }
 
+int32_t orc_adaptive(const float* X, int64_t n, int32_t m, const float* q,
+                     const orc_adaptive_params* p, const int32_t* replay,
+                     int64_t* out_idx, int32_t* code, double* S, int32_t* T,
+                     orc_adaptive_stats* st) {
+    if (p->storage == ORC_STORE_F32)
+        return adaptive_core(X, X, 0.0, n, m, q, p, replay, out_idx, code, S, T, st);
+    float* G = (float*)malloc(sizeof(float) * (size_t)n * (size_t)m);
+    double emax = orc_quantize(p->storage, X, n, m, G, NULL);
+    int32_t rc = adaptive_core(X, G, emax, n, m, q, p, replay, out_idx, code, S, T, st);
+    free(G);
+    return rc;
+}
+
 int32_t orc_adaptive_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
                            const orc_adaptive_params* p, const int32_t* replay,
                            int64_t* out_idx, int32_t* codes, double* S, int32_t* T,
                            orc_adaptive_stats* st, int32_t threads) {
     const int64_t kh = (int64_t)p->k + p->h;
+    const float* G = X;
+    float* Gq = NULL;
+    double emax = 0.0;
+    if (p->storage != ORC_STORE_F32) {
+        Gq = (float*)malloc(sizeof(float) * (size_t)n * (size_t)m);
+        emax = orc_quantize(p->storage, X, n, m, Gq, NULL);
+        G = Gq;
+    }
     int32_t bad = 0;
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
@@ -376,11 +465,11 @@ int32_t orc_adaptive_batch(const float* X, int64_t n, int32_t m, const float* Q,
         orc_adaptive_params pq = *p;
         pq.qid = p->qid + (uint64_t)qi;
         size_t off = (size_t)qi * (size_t)n;
-        bad |= orc_adaptive(X, n, m, Q + (size_t)qi * (size_t)m, &pq,
-                            replay ? replay + off : NULL, out_idx + (size_t)qi * (size_t)kh,
-                            codes ? codes + off : NULL, S ? S + off : NULL, T ? T + off : NULL,
-                            st + qi);
+        bad |= adaptive_core(X, G, emax, n, m, Q + (size_t)qi * (size_t)m, &pq,
+                             replay ? replay + off : NULL, out_idx + (size_t)qi * (size_t)kh,
+                             codes ? codes + off : NULL, S ? S + off : NULL, T ? T + off : NULL, st + qi);
     }
+    free(Gq);
     return bad;
 }
 

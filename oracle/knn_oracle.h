@@ -49,7 +49,19 @@ typedef struct {
     int32_t B0, B, grow;  /* round schedule: B_0 = B0; later B_r = B, or max(B, T) if grow */
     uint64_t seed, qid, mask_p, mask_q;
     double tol;           /* relative width of the near-threshold band used in replay */
+    int32_t storage;      /* ORC_STORE_*: the values the samples are taken from */
 } orc_adaptive_params;
+
+/* Storage of the gathered copy: FP32 itself, BF16 (round to nearest even),
+ * or FP8 e4m3 with a per-row scale max|x_i| / 448. */
+enum { ORC_STORE_F32 = 0, ORC_STORE_BF16 = 1, ORC_STORE_FP8 = 2 };
+
+/* Dequantised copies: out = bf16(x) as float; or, per row, s = max|x|/448
+ * (1 if the row is zero) and out = fl32(s * e4m3(fl32(x / s))). Returns the
+ * largest |out - x| (exact). scale may be NULL. */
+double orc_quantize(int32_t storage, const float* X, int64_t n, int32_t m, float* out, float* scale);
+float orc_round_bf16(float x);
+float orc_round_e4m3(float x);
 
 typedef struct {
     int64_t evals;        /* coordinate evaluations: samples drawn + m per exact distance */

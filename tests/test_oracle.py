@@ -304,3 +304,62 @@ def test_sequential_and_batched_same_order_of_cost():
     r = oracle.adaptive(X, q, p)
     ev_bat = r["stats"][0]["evals"]
     assert 0.1 < ev_bat / ev_seq < 10
+
+
+# ------------------------------------------------------- stored copies (BF16 / FP8)
+
+def test_bf16_rounding_matches_torch():
+    import torch
+    rng = np.random.default_rng(3)
+    x = np.concatenate([rng.standard_normal(20000) * 10 ** rng.uniform(-30, 30, 20000),
+                        np.array([0.0, -0.0, 1.0, 1.00390625, 1.01171875, 3.0e38, 1e-40])]).astype(np.float32)
+    ours = np.array([oracle.lib().orc_round_bf16(float(v)) for v in x], dtype=np.float32)
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(ours.view(np.uint32), ref.view(np.uint32))
+
+
+def test_e4m3_rounding_matches_torch():
+    import torch
+    rng = np.random.default_rng(4)
+    x = np.concatenate([rng.uniform(-448, 448, 20000), rng.uniform(-0.05, 0.05, 5000),
+                        np.array([2 ** -10, 3 * 2 ** -11, 2 ** -9, 447.9, 448.0, 15.5, 17.0, -2 ** -10])]
+                       ).astype(np.float32)
+    ours = np.array([oracle.lib().orc_round_e4m3(float(v)) for v in x], dtype=np.float32)
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+    np.testing.assert_array_equal(ours, ref)
+
+
+def test_quantize_rows_and_error():
+    X, _ = synth.pixel_mixture(300, 50, 1, seed=2)
+    X[7] = 0.0
+    for st in ("bf16", "fp8"):
+        G, scale, emax = oracle.quantize(X, st)
+        assert emax == np.abs(G.astype(np.float64) - X).max()
+        if st == "fp8":
+            mx = np.abs(X).max(1)
+            np.testing.assert_array_equal(scale, np.where(mx > 0, (mx / np.float32(448)).astype(np.float32), 1))
+            assert np.all(np.abs(G) <= np.abs(X).max(1, keepdims=True) * (1 + 2 ** -20))
+            assert np.all(G[7] == 0)
+    assert oracle.quantize(X, "bf16")[2] <= 2 ** -9 * np.abs(X).max()
+
+
+def test_lossless_bf16_copy_reproduces_the_fp32_run():
+    """Integers 0..255 are exact in BF16: the copy equals the data, the
+    widening is zero, and every decision must be the FP32 run's."""
+    X, Q, _ = synth.gap_planted(3000, 64, 3, 5, [3.0, 1.5, 1.05], seed=6, background="int255")
+    a = oracle.adaptive(X, Q, _params(c_alpha=1e-3, storage="f32"))
+    b = oracle.adaptive(X, Q, _params(c_alpha=1e-3, storage="bf16"))
+    np.testing.assert_array_equal(a["code"], b["code"])
+    np.testing.assert_array_equal(a["idx"], b["idx"])
+
+
+def test_stored_copies_keep_the_guarantee():
+    """With the bound widened by the copy's error, Theorem 1's containment
+    still holds (binary data: FP8 and BF16 are lossy only through the scale)."""
+    X, Q, _ = synth.gaussian_planted(1500, 128, 4, nq=4, seed=8)
+    ti, _ = oracle.exact_knn(X, Q, 4)
+    for st in ("bf16", "fp8"):
+        r = oracle.adaptive(X, Q, _params(k=4, bound="footnote", storage=st))
+        for q in range(4):
+            c = r["stats"][q]["count"]
+            assert c <= 8 and set(ti[q]) <= set(r["idx"][q][:c])
