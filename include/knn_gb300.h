@@ -50,6 +50,13 @@ typedef enum {
  *   EXP       sqrt(C_alpha log(1 + (1 + log u) n / delta) / u)   (Section 5)       */
 typedef enum { KNN_BOUND_FOOTNOTE = 0, KNN_BOUND_LEMMA = 1, KNN_BOUND_EXP = 2 } knn_bound;
 
+/* Element type of the copy of the data the adaptive rounds gather from. */
+typedef enum {
+    KNN_STORE_F32 = 0,   /* the FP32 data itself */
+    KNN_STORE_BF16 = 1,  /* bfloat16, round to nearest even */
+    KNN_STORE_FP8 = 2    /* FP8 e4m3, per-row scale s_i = max_j |x_ij| / 448 (1 for a zero row) */
+} knn_storage;
+
 /* Options of knn_adaptive. Fill with knn_opts_default() and change fields. */
 typedef struct {
     int32_t h;          /* extra set size: returned set has at most k+h points; -1 means h = k */
@@ -138,6 +145,37 @@ knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const floa
                                 int32_t k, double delta, uint64_t seed, const knn_opts* opts,
                                 int64_t* out_idx, int32_t* out_count, int64_t* out_evals,
                                 int32_t* out_rounds, int32_t* log_code, float* log_S, void* stream);
+
+/*
+ * Datasets: a resident copy of X with everything the rounds need precomputed
+ * once -- the data range (finite values; non-finite data flagged) and, on
+ * request, BF16 and FP8 copies with their largest element error e.
+ * (Mixed-precision storage is not in the paper; it cuts gather bytes. The
+ * bounds stay valid: a sample of a copy differs from the data's sample by at
+ * most eps = e (2 span + e), so the interval width becomes
+ * (span + 2e)^2 alpha(T) + eps, and an exact round of a copy keeps width eps.
+ * The returned candidates are then reranked on the FP32 data.)
+ *
+ * knn_dataset_create: X is the caller's n x m FP32 device matrix and must
+ *   stay alive and unchanged while the dataset is used (FP32 rounds and
+ *   reranks read it). `copies` is a bit mask of (1 << KNN_STORE_BF16) and
+ *   (1 << KNN_STORE_FP8). Allocates the copies with cudaMalloc, builds them
+ *   on `stream` and waits for them. *out receives the handle.
+ * knn_dataset_destroy: frees the copies (waits for the device first).
+ * knn_dataset_error: largest |copy - X| of a copy (host value; 0 for F32).
+ * knn_adaptive_ds: knn_adaptive over the dataset, gathering from the chosen
+ *   copy (same outputs, same workspace size as knn_adaptive).
+ */
+typedef struct knn_dataset knn_dataset;
+knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, int32_t copies, void* stream,
+                              knn_dataset** out);
+knn_status knn_dataset_destroy(knn_dataset* ds);
+knn_status knn_dataset_error(const knn_dataset* ds, int32_t storage, float* out_error);
+knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, const float* Q, int32_t nq,
+                           int32_t k, double delta, uint64_t seed, const knn_opts* opts,
+                           int64_t* out_idx, int32_t* out_count, int64_t* out_evals,
+                           int32_t* out_rounds, int32_t* log_code, float* log_S,
+                           void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * knn_rerank -- exact distances of candidate points, then top-k.

@@ -1,645 +1,11 @@
-// adaptive.cu -- the batched adaptive rounds of the k-NN method of LeJeune,
-// Baraniuk and Heckel (AISTATS 2019), as one persistent kernel.
-//
-// One CTA owns one query at a time and runs all of its rounds; CTAs take the
-// next query from a device work queue, so queries of uneven difficulty share
-// the GPU without host round trips. Per round and query:
-//   gather    every active point draws B_r coordinates (Philox4x64-10) and
-//             adds the squared differences to its FP32 Kahan sum S, or takes
-//             its exact distance once the count would reach m (Algorithm 1);
-//             the same pass histograms the new sums (bits 31..20 of the key);
-//   select    the k+1 smallest sums among active points (radix select that
-//             finishes in shared memory);
-//   bounds    UCB/LCB = S/T +- span^2 alpha(T) (Section 4, footnote and
-//             Lemma forms, or the Section 5 form with C_alpha);
-//   decide    tau_U = k-th smallest UCB over active and accepted points,
-//             tau_L = min((k+1)-th smallest LCB, smallest eliminated LCB);
-//             LCB > tau_U eliminates, UCB < tau_L accepts (the batched form
-//             of Eq. d_ind and Eq. termination);
-//   compact   order-preserving prefix-sum compaction of the survivors into the
-//             other half of the CTA's ping-pong buffers.
-// Active points of a query all carry the same sample count T, so T is a
-// per-round scalar, and the per-point state is (id, S, Kahan term).
-#include <cfloat>
-#include <cmath>
+// adaptive.cu -- C-ABI entry points of the adaptive rounds over an FP32
+// matrix: knn_adaptive (workspace from the caller or stream-ordered) and
+// knn_adaptive_noalloc (scratch in a fixed device array). The kernel itself
+// is in adaptive_kernel.cuh.
 #include <mutex>
 #include <string>
-#include <vector>
 
-#include "knn_common.cuh"
-#include "knn_internal.h"
-
-namespace knn {
-
-struct AdaptiveArgs {
-  const float* X;
-  const float* Q;
-  int64_t n;
-  int32_t m;
-  int32_t nq;
-  int32_t k, h;
-  int32_t bound;
-  float a_c0, a_c1, c_alpha;  // host-precomputed constants of alpha(u)
-  int32_t B0, B, grow;
-  uint64_t seed, qid_base, mask_p, mask_q;
-  const uint32_t* xrange;  // ordered keys of min(X), max(X) over finite values; [2] non-finite flag
-  int32_t* ws_ids;
-  float* ws_S;
-  float* ws_C;
-  int32_t* ws_acc_id;
-  float* ws_acc_d;
-  float* ws_acc_U;
-  float* ws_acc_L;
-  int32_t acc_cap;
-  int32_t* queue;
-  int64_t* out_idx;
-  int32_t* out_count;
-  int64_t* out_evals;
-  int32_t* out_rounds;
-  int32_t* log_code;
-  float* log_S;
-  int32_t vec4;  // rows are 16-byte aligned and m % 4 == 0
-};
-
-constexpr int kIPT = 4;  // consecutive slots per thread in the decide pass
-
-template <int NT>
-struct AdaptiveShared {
-  BlockScratch<NT> bs;
-  SelectShared ss;
-  int q;
-  int nacc_add;
-  int bad;
-  float tauU, tauL;
-};
-
-// alpha(u) in normalised units. c0/c1 carry the delta- and n-dependent
-// constants computed on the host in double precision.
-__device__ __forceinline__ float alpha_of(const AdaptiveArgs& a, int64_t u) {
-  const float uu = (float)u;
-  const float lu = logf(uu);
-  if (a.bound == KNN_BOUND_FOOTNOTE) {
-    // beta = log(1/d') + 3 log log(1/d') + 1.5 log(1 + log u)
-    const float beta = a.a_c0 + 1.5f * logf(1.0f + lu);
-    return sqrtf(2.0f * beta / uu);
-  }
-  if (a.bound == KNN_BOUND_LEMMA) {
-    // beta = 2 log(125 log(1.12 u) / d') = 2 (log(125/d') + log log(1.12 u))
-    const float beta = 2.0f * (a.a_c0 + logf(logf(1.12f * uu)));
-    return sqrtf(2.0f * beta / uu);
-  }
-  // sqrt(C log(1 + (1 + log u) n / delta) / u), c1 = n / delta
-  return sqrtf(a.c_alpha * log1pf((1.0f + lu) * a.a_c1) / uu);
-}
-
-// Value of rank `kth` (1-based) in the union of the ascending array A[0..na)
-// and the unordered array Bv[0..nb). Every thread gets the result.
-template <int NT>
-__device__ float kth_of_union(const float* A, int na, const float* Bv, int nb, int kth, float* out) {
-  for (int t = threadIdx.x; t < na + nb; t += NT) {
-    const float v = t < na ? A[t] : Bv[t - na];
-    int lo = 0, hi = na;  // lower bound of v in A
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (A[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    int lt = lo;
-    hi = na;  // upper bound of v in A
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (A[mid] <= v) lo = mid + 1; else hi = mid;
-    }
-    int le = lo;
-    for (int b = 0; b < nb; ++b) {
-      const float x = Bv[b];
-      lt += x < v;
-      le += x <= v;
-    }
-    if (lt < kth && kth <= le) *out = v;
-  }
-  __syncthreads();
-  const float r = *out;
-  __syncthreads();
-  return r;
-}
-
-// Sampled gather: slots [0, nact) of the active list, samples T .. Tn-1.
-template <int NT>
-__device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, int q, int r, int nact, int64_t T, int64_t Tn,
-                                               const float* qs, const int32_t* idc, float* Sc, float* Cc,
-                                               uint32_t* hist) {
-  const int m = a.m;
-  const uint64_t blo = (uint64_t)T >> 3, bhi = (uint64_t)(Tn - 1) >> 3;
-  const int nblk = (int)(bhi - blo + 1);
-  int G = 1;
-  while (G < nblk && G < 32) G <<= 1;
-  const int lg = __ffs(G) - 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int grp = lane >> lg, gl = lane & (G - 1);
-  const int ppw = 32 >> lg;
-  const uint64_t qfield = (a.qid_base + (uint64_t)q) & a.mask_q;
-  for (int base = warp * ppw; base < nact; base += (NT / 32) * ppw) {
-    const int sidx = base + grp;
-    const bool valid = sidx < nact;
-    float part = 0.0f;
-    if (valid) {
-      const int id = (r == 0) ? sidx : idc[sidx];
-      const float* xr = a.X + (size_t)id * (size_t)m;
-      const uint64_t pfield = (uint64_t)id & a.mask_p;
-      for (uint64_t b = blo + gl; b <= bhi; b += G) {
-        const Philox4x64 ph = philox4x64_10(b, pfield, qfield, 0, a.seed, 0);
-        const int64_t s0 = (int64_t)(b << 3);
-        float xv[8];
-        int jj[8];
-        bool ok[8];
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          const int64_t s = s0 + w;
-          ok[w] = (s >= T) && (s < Tn);
-          jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
-          xv[w] = ok[w] ? __ldg(xr + jj[w]) : 0.0f;
-        }
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          if (ok[w]) {
-            const float d = xv[w] - qs[jj[w]];
-            part = fmaf(d, d, part);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1)
-      if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (valid && gl == 0) {
-      float S;
-      if (r == 0) {
-        S = part;
-      } else {
-        // Kahan-compensated running sum
-        const float S0 = Sc[sidx], c0 = Cc[sidx];
-        const float y = part - c0;
-        const float t = S0 + y;
-        Cc[sidx] = (t - S0) - y;
-        S = t;
-      }
-      Sc[sidx] = S;
-      atomicAdd(&hist[f2key(S) >> 20], 1u);
-    }
-  }
-}
-
-// Exact round: one warp per active point, the full row.
-template <int NT>
-__device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int nact, const float* qs,
-                                             const int32_t* idc, float* Sc, uint32_t* hist) {
-  const int m = a.m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int sidx = warp; sidx < nact; sidx += NT / 32) {
-    const int id = (r == 0) ? sidx : idc[sidx];
-    const float* xr = a.X + (size_t)id * (size_t)m;
-    float part = 0.0f;
-    if (a.vec4) {
-#pragma unroll 4
-      for (int j = lane * 4; j < m; j += 128) {
-        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr + j));
-        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
-        float d = x4.x - q4.x;
-        part = fmaf(d, d, part);
-        d = x4.y - q4.y;
-        part = fmaf(d, d, part);
-        d = x4.z - q4.z;
-        part = fmaf(d, d, part);
-        d = x4.w - q4.w;
-        part = fmaf(d, d, part);
-      }
-    } else {
-#pragma unroll 4
-      for (int j = lane; j < m; j += 32) {
-        const float d = __ldg(xr + j) - qs[j];
-        part = fmaf(d, d, part);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == 0) {
-      Sc[sidx] = part;
-      atomicAdd(&hist[f2key(part) >> 20], 1u);
-    }
-  }
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) {
-  extern __shared__ __align__(16) uint8_t smem_raw[];
-  __shared__ AdaptiveShared<NT> sh;
-  const int m = a.m;
-  const int mpad = (m + 3) & ~3;
-  float* qs = reinterpret_cast<float*>(smem_raw);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(qs + mpad);
-  uint32_t* buf = hist + kHistBins;
-  float* actU = reinterpret_cast<float*>(buf + kSelCap);
-  float* actL = actU + (kMaxKH + 4);
-  int32_t* oid = reinterpret_cast<int32_t*>(actL + (kMaxKH + 4));
-  float* tmpS = actU;                              // reused in the output phase
-  int32_t* tmpI = reinterpret_cast<int32_t*>(actL);
-
-  const int tid = threadIdx.x;
-  const int64_t n = a.n;
-  const int k = a.k, kh = a.k + a.h;
-  const size_t slot = blockIdx.x;
-  // ping-pong halves: buffer b of this CTA starts at base + b * n
-  int32_t* const ids0 = a.ws_ids + slot * 2 * (size_t)n;
-  float* const S0 = a.ws_S + slot * 2 * (size_t)n;
-  float* const C0 = a.ws_C + slot * 2 * (size_t)n;
-  int32_t* acc_id = a.ws_acc_id + slot * (size_t)a.acc_cap;
-  float* acc_d = a.ws_acc_d + slot * (size_t)a.acc_cap;
-  float* acc_U = a.ws_acc_U + slot * (size_t)a.acc_cap;
-  float* acc_L = a.ws_acc_L + slot * (size_t)a.acc_cap;
-
-  for (;;) {
-    if (tid == 0) sh.q = atomicAdd(a.queue, 1);
-    __syncthreads();
-    const int q = sh.q;
-    if (q >= a.nq) break;
-    int64_t* oidx = a.out_idx + (size_t)q * kh;
-    int32_t* lcode = a.log_code ? a.log_code + (size_t)q * (size_t)n : nullptr;
-    float* lS = a.log_S ? a.log_S + (size_t)q * (size_t)n : nullptr;
-
-    // ---- query row into shared memory; span of the normalisation (Section 3)
-    const float* qr = a.Q + (size_t)q * m;
-    float qmin = FLT_MAX, qmax = -FLT_MAX;
-    int bad = 0;
-    for (int j = tid; j < m; j += NT) {
-      const float v = qr[j];
-      qs[j] = v;
-      bad |= !isfinite(v);
-      qmin = fminf(qmin, v);
-      qmax = fmaxf(qmax, v);
-    }
-    for (int j = m + tid; j < mpad; j += NT) qs[j] = 0.0f;
-    bad = __syncthreads_or(bad);
-    qmin = block_min<NT>(qmin, sh.bs);
-    qmax = block_max<NT>(qmax, sh.bs);
-    const float xmin = key2f(a.xrange[0]), xmax = key2f(a.xrange[1]);
-    bad |= a.xrange[2] != 0u;  // non-finite data (flagged by the range pass)
-    const float span = fmaxf(xmax, qmax) - fminf(xmin, qmin);
-    const float span2 = span * span;
-    if (bad || !isfinite(span2)) {
-      for (int t = tid; t < kh; t += NT) oidx[t] = -1;
-      if (tid == 0) {
-        a.out_count[q] = 0;
-        a.out_evals[q] = 0;
-        if (a.out_rounds) a.out_rounds[q] = 0;
-      }
-      __syncthreads();
-      continue;
-    }
-    if (n <= kh) {  // every point is a candidate
-      for (int t = tid; t < kh; t += NT) oidx[t] = t < n ? t : -1;
-      if (lcode)
-        for (int64_t i = tid; i < n; i += NT) {
-          lcode[i] = 0;
-          if (lS) lS[i] = 0.0f;
-        }
-      if (tid == 0) {
-        a.out_count[q] = (int32_t)n;
-        a.out_evals[q] = 0;
-        if (a.out_rounds) a.out_rounds[q] = 0;
-      }
-      __syncthreads();
-      continue;
-    }
-
-    int nact = (int)n, nacc = 0, cur = 0, r = 0, term = 0;
-    int64_t T = 0, evals = 0;
-    float min_elim = INFINITY;
-    for (;;) {
-      const int64_t Br = (r == 0) ? a.B0 : (a.grow ? (T > a.B ? T : (int64_t)a.B) : (int64_t)a.B);
-      const bool exact = T + Br >= m;
-      const int64_t Tn = exact ? m : T + Br;
-      const int32_t* idc = ids0 + (size_t)cur * n;
-      float* Sc = S0 + (size_t)cur * n;
-      float* Cc = C0 + (size_t)cur * n;
-      for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
-      __syncthreads();
-      if (exact)
-        gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
-      else
-        gather_sampled<NT>(a, q, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
-      __syncthreads();
-      evals += (int64_t)nact * (exact ? (int64_t)m : Br);
-      const float w = exact ? 0.0f : span2 * alpha_of(a, Tn);
-      const float Tf = (float)Tn;
-
-      // ---- thresholds
-      const int kk = min(k + 1, nact);
-      select_smallest<NT>([&](int i) { return f2key(Sc[i]); }, nact, kk, hist, buf, sh.ss, sh.bs);
-      for (int j = tid; j < kk; j += NT) {
-        const float d = key2f(buf[j]) / Tf;
-        actU[j] = d + w;
-        actL[j] = d - w;
-      }
-      if (tid == 0) sh.nacc_add = 0;
-      __syncthreads();
-      const float tauU = kth_of_union<NT>(actU, min(k, nact), acc_U, nacc, k, &sh.tauU);
-      const float tauL = fminf(kth_of_union<NT>(actL, kk, acc_L, nacc, k + 1, &sh.tauL), min_elim);
-
-      // ---- decide + compact (order-preserving)
-      int32_t* idn = ids0 + (size_t)(cur ^ 1) * n;
-      float* Sn = S0 + (size_t)(cur ^ 1) * n;
-      float* Cn = C0 + (size_t)(cur ^ 1) * n;
-      float rmin = INFINITY;
-      int out_base = 0;
-      for (int cb = 0; cb < nact; cb += NT * kIPT) {
-        int myid[kIPT];
-        float myS[kIPT], myC[kIPT];
-        bool keep[kIPT];
-        int cnt = 0;
-#pragma unroll
-        for (int e = 0; e < kIPT; ++e) {
-          const int s = cb + tid * kIPT + e;
-          keep[e] = false;
-          myid[e] = 0;
-          myS[e] = 0.0f;
-          myC[e] = 0.0f;
-          if (s < nact) {
-            const int id = (r == 0) ? s : idc[s];
-            const float S = Sc[s];
-            const float c = (r == 0 || exact) ? 0.0f : Cc[s];
-            const float d = S / Tf;
-            const float U = d + w, L = d - w;
-            if (L > tauU) {
-              rmin = fminf(rmin, L);
-              if (lcode) {
-                lcode[id] = 4 * r + 1;
-                if (lS) lS[id] = S;
-              }
-            } else if (U < tauL) {
-              const int sl = nacc + atomicAdd(&sh.nacc_add, 1);
-              if (sl < a.acc_cap) {
-                acc_id[sl] = id;
-                acc_d[sl] = d;
-                acc_U[sl] = U;
-                acc_L[sl] = L;
-              }
-              if (lcode) {
-                lcode[id] = 4 * r + 2;
-                if (lS) lS[id] = S;
-              }
-            } else {
-              keep[e] = true;
-              ++cnt;
-            }
-            myid[e] = id;
-            myS[e] = S;
-            myC[e] = c;
-          }
-        }
-        int total;
-        int pos = out_base + block_exclusive_scan<NT>(cnt, sh.bs, &total);
-#pragma unroll
-        for (int e = 0; e < kIPT; ++e) {
-          if (keep[e]) {
-            idn[pos] = myid[e];
-            Sn[pos] = myS[e];
-            Cn[pos] = myC[e];
-            ++pos;
-          }
-        }
-        out_base += total;
-      }
-      rmin = block_min<NT>(rmin, sh.bs);  // also orders sh.nacc_add
-      nacc = min(nacc + sh.nacc_add, a.acc_cap);
-      nact = out_base;
-      min_elim = fminf(min_elim, rmin);
-      T = Tn;
-      cur ^= 1;
-      if (nact + nacc <= kh) term = 1;
-      else if (nacc >= k) term = 2;
-      else if (exact) term = 3;
-      if (term) break;
-      ++r;
-      __syncthreads();
-    }
-
-    // ---- output: accepted by (estimate, index), then active by (estimate, index)
-    const int32_t* idf = ids0 + (size_t)cur * n;
-    const float* Sf = S0 + (size_t)cur * n;
-    const int nacc_o = min(nacc, kh);
-    const int rem = kh - nacc_o;
-    const int nact_o = min(nact, rem);
-    for (int i = tid; i < nacc; i += NT) {
-      const float di = acc_d[i];
-      const int ii = acc_id[i];
-      int rank = 0;
-      for (int j = 0; j < nacc; ++j) {
-        const float dj = acc_d[j];
-        rank += (dj < di) || (dj == di && acc_id[j] < ii);
-      }
-      if (rank < kh) oid[rank] = ii;
-    }
-    if (nact_o > 0) {
-      if (nact <= rem) {
-        for (int i = tid; i < nact; i += NT) {
-          tmpS[i] = Sf[i];
-          tmpI[i] = idf[i];
-        }
-      } else {
-        for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
-        __syncthreads();
-        for (int i = tid; i < nact; i += NT) atomicAdd(&hist[f2key(Sf[i]) >> 20], 1u);
-        __syncthreads();
-        select_smallest<NT>([&](int i) { return f2key(Sf[i]); }, nact, rem, hist, buf, sh.ss, sh.bs);
-        const uint32_t kstar = buf[rem - 1];
-        int nless = 0;  // keys of buf below kstar (buf is ascending)
-        {
-          int lo = 0, hi = rem;
-          while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (buf[mid] < kstar) lo = mid + 1; else hi = mid;
-          }
-          nless = lo;
-        }
-        const int need_ties = rem - nless;
-        if (tid == 0) sh.ss.cnt = 0;
-        __syncthreads();
-        int tie_base = 0;
-        for (int cb = 0; cb < nact; cb += NT) {
-          const int s = cb + tid;
-          uint32_t key = 0xFFFFFFFFu;
-          if (s < nact) key = f2key(Sf[s]);
-          const bool less = s < nact && key < kstar;
-          const bool tie = s < nact && key == kstar;
-          if (less) {
-            const int p = atomicAdd(&sh.ss.cnt, 1);
-            tmpS[p] = Sf[s];
-            tmpI[p] = idf[s];
-          }
-          int total;
-          const int tr = tie_base + block_exclusive_scan<NT>(tie ? 1 : 0, sh.bs, &total);
-          if (tie && tr < need_ties) {
-            tmpS[nless + tr] = Sf[s];
-            tmpI[nless + tr] = idf[s];
-          }
-          tie_base += total;
-        }
-      }
-      __syncthreads();
-      for (int i = tid; i < nact_o; i += NT) {
-        const float si = tmpS[i];
-        const int ii = tmpI[i];
-        int rank = 0;
-        for (int j = 0; j < nact_o; ++j) {
-          const float sj = tmpS[j];
-          rank += (sj < si) || (sj == si && tmpI[j] < ii);
-        }
-        oid[nacc_o + rank] = ii;
-      }
-    }
-    __syncthreads();
-    const int count = nacc_o + nact_o;
-    for (int t = tid; t < kh; t += NT) oidx[t] = t < count ? (int64_t)oid[t] : -1;
-    if (lcode)
-      for (int i = tid; i < nact; i += NT) {
-        lcode[idf[i]] = 4 * r + 0;
-        if (lS) lS[idf[i]] = Sf[i];
-      }
-    if (tid == 0) {
-      a.out_count[q] = count;
-      a.out_evals[q] = evals;
-      if (a.out_rounds) a.out_rounds[q] = r + 1;
-    }
-    __syncthreads();
-  }
-}
-
-// Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and
-// xr[2] = 1 if any element is NaN or infinite.
-__global__ void minmax_kernel(const float* __restrict__ X, size_t count, uint32_t* xr) {
-  uint32_t lo = 0xFFFFFFFFu, hi = 0u, bad = 0u;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
-    const float v = __ldg(X + i);
-    if (isfinite(v)) {
-      const uint32_t key = f2key(v);
-      lo = min(lo, key);
-      hi = max(hi, key);
-    } else {
-      bad = 1u;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(&xr[0], lo);
-    atomicMax(&xr[1], hi);
-    if (bad) atomicOr(&xr[2], 1u);
-  }
-}
-
-// --------------------------------------------------------------- host side
-
-constexpr int kAdaptiveNT = 512;
-
-static size_t adaptive_smem_bytes(int m) {
-  const size_t mpad = (size_t)((m + 3) & ~3);
-  return mpad * 4 + (size_t)kHistBins * 4 + (size_t)kSelCap * 4 + 2 * (size_t)(kMaxKH + 4) * 4 +
-         (size_t)kMaxKH * 4;
-}
-
-struct AdaptivePlan {
-  int grid = 0;
-  int acc_cap = 0;
-  size_t smem = 0;
-};
-
-static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* o, AdaptivePlan* p) {
-  DeviceInfo di;
-  knn_status s = device_info(&di);
-  if (s != KNN_OK) return s;
-  p->smem = adaptive_smem_bytes(m);
-  s = cuda_check(cudaFuncSetAttribute(adaptive_rounds_kernel<kAdaptiveNT>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
-                 "cudaFuncSetAttribute(adaptive)");
-  if (s != KNN_OK) return s;
-  int per_sm = 0;
-  s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adaptive_rounds_kernel<kAdaptiveNT>,
-                                                                 kAdaptiveNT, p->smem),
-                 "occupancy(adaptive)");
-  if (s != KNN_OK) return s;
-  if (per_sm < 1) {
-    set_error("adaptive kernel does not fit on an SM");
-    return KNN_EUNSUPPORTED;
-  }
-  int grid = per_sm * di.sms;
-  if (o && o->max_ctas > 0 && o->max_ctas < grid) grid = o->max_ctas;
-  if (grid > nq) grid = nq;
-  if (grid < 1) grid = 1;
-  p->grid = grid;
-  p->acc_cap = 2 * k + 2;
-  (void)n;
-  return KNN_OK;
-}
-
-struct AdaptiveCarve {
-  uint32_t* xrange;
-  int32_t* queue;
-  int32_t* ids;
-  float* S;
-  float* C;
-  int32_t* acc_id;
-  float* acc_d;
-  float* acc_U;
-  float* acc_L;
-};
-
-static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, AdaptiveCarve* out) {
-  AdaptiveCarve c;
-  c.xrange = cv.take<uint32_t>(3);
-  c.queue = cv.take<int32_t>(1);
-  const size_t per = (size_t)p.grid * 2 * (size_t)n;
-  c.ids = cv.take<int32_t>(per);
-  c.S = cv.take<float>(per);
-  c.C = cv.take<float>(per);
-  const size_t acc = (size_t)p.grid * (size_t)p.acc_cap;
-  c.acc_id = cv.take<int32_t>(acc);
-  c.acc_d = cv.take<float>(acc);
-  c.acc_U = cv.take<float>(acc);
-  c.acc_L = cv.take<float>(acc);
-  if (out) *out = c;
-  return cv.off;
-}
-
-static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double delta, const knn_opts& o) {
-  if (n < 1 || n >= (int64_t)1 << 31) return set_error("n must be in [1, 2^31)"), KNN_EINVAL;
-  if (m < 1 || m > kMaxM) return set_error("m must be in [1, 16384]"), KNN_EINVAL;
-  if (nq < 0) return set_error("nq must be >= 0"), KNN_EINVAL;
-  if (k < 1 || k > n) return set_error("k must be in [1, n]"), KNN_EINVAL;
-  if (o.h < 0 || (int64_t)k + o.h > kMaxKH) return set_error("need h >= 0 and k + h <= 1024"), KNN_EINVAL;
-  if (!(delta > 0.0 && delta < 1.0)) return set_error("delta must be in (0, 1)"), KNN_EINVAL;
-  if (o.bound < 0 || o.bound > 2) return set_error("unknown bound form"), KNN_EINVAL;
-  if (o.bound == KNN_BOUND_FOOTNOTE && !(delta / (double)n < std::exp(-1.0)))
-    return set_error("footnote bound needs delta/n < 1/e"), KNN_EINVAL;
-  if (o.bound == KNN_BOUND_EXP && !(o.c_alpha > 0.0)) return set_error("c_alpha must be > 0"), KNN_EINVAL;
-  if (o.B0 < 1 || o.B < 1) return set_error("B0 and B must be >= 1"), KNN_EINVAL;
-  if (o.grow != 0 && o.grow != 1) return set_error("grow must be 0 or 1"), KNN_EINVAL;
-  return KNN_OK;
-}
-
-static knn_opts resolve(const knn_opts* opts, int32_t k) {
-  knn_opts o;
-  knn_opts_default(&o);
-  if (opts) o = *opts;
-  if (o.h < 0) o.h = k;
-  return o;
-}
-
-}  // namespace knn
+#include "adaptive_kernel.cuh"
 
 using namespace knn;
 
@@ -661,7 +27,7 @@ extern "C" void knn_opts_default(knn_opts* o) {
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {
   const knn_opts o = resolve(opts, k);
   AdaptivePlan p;
-  if (plan_adaptive(n, m, nq, k, &o, &p) != KNN_OK) return 0;
+  if (plan_adaptive<ElemF32>(n, m, nq, k, &o, &p) != KNN_OK) return 0;
   Carve cv;
   return carve_adaptive(cv, n, p, nullptr) + 256;
 }
@@ -685,7 +51,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   }
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   AdaptivePlan p;
-  s = plan_adaptive(n, m, nq, k, &o, &p);
+  s = plan_adaptive<ElemF32>(n, m, nq, k, &o, &p);
   if (s != KNN_OK) return s;
   Carve measure;
   const size_t need = carve_adaptive(measure, n, p, nullptr) + 256;
@@ -720,7 +86,9 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   }
 
   AdaptiveArgs a;
-  a.X = X;
+  a.G = X;
+  a.gscale = nullptr;
+  a.emax = nullptr;
   a.Q = Q;
   a.n = n;
   a.m = m;
@@ -761,8 +129,8 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.out_rounds = out_rounds;
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
-  a.vec4 = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
-  adaptive_rounds_kernel<kAdaptiveNT><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
+  a.vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  adaptive_rounds_kernel<kAdaptiveNT, ElemF32><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
   s = cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
   ws.release();
   return s;
@@ -825,7 +193,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   }
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   AdaptivePlan p;
-  s = plan_adaptive(n, m, nq, k, &o, &p);
+  s = plan_adaptive<ElemF32>(n, m, nq, k, &o, &p);
   if (s != KNN_OK) return s;
   // as many resident CTAs as the fixed scratch holds (each needs 24 n bytes)
   for (;;) {
@@ -864,7 +232,9 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
     if (s != KNN_OK) return s;
   }
   AdaptiveArgs a;
-  a.X = X;
+  a.G = X;
+  a.gscale = nullptr;
+  a.emax = nullptr;
   a.Q = Q;
   a.n = n;
   a.m = m;
@@ -905,7 +275,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.out_rounds = out_rounds;
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
-  a.vec4 = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
-  adaptive_rounds_kernel<kAdaptiveNT><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
+  a.vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  adaptive_rounds_kernel<kAdaptiveNT, ElemF32><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
   return cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
 }

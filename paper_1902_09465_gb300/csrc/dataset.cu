@@ -1,0 +1,259 @@
+// dataset.cu -- resident datasets: the data range computed once, BF16 and
+// FP8-e4m3 (per-row scale) copies with their largest element error, and the
+// adaptive rounds over a chosen copy (knn_adaptive_ds).
+#include <cuda_bf16.h>
+
+#include <string>
+
+#include "adaptive_kernel.cuh"
+
+struct knn_dataset {
+  const float* X = nullptr;
+  int64_t n = 0;
+  int32_t m = 0;
+  int32_t copies = 0;
+  int device = 0;
+  uint32_t* range = nullptr;  // [3]: min key, max key (finite values), non-finite flag
+  uint16_t* xb = nullptr;     // BF16 copy
+  uint8_t* x8 = nullptr;      // FP8 e4m3 copy
+  float* scale8 = nullptr;    // FP8 per-row scale
+  unsigned* emax = nullptr;   // [3]: largest |copy - X| per storage, as float bits
+  float emax_host[3] = {0.0f, 0.0f, 0.0f};
+};
+
+namespace knn {
+
+// BF16 copy (round to nearest even) and its largest element error.
+static __global__ void quantize_bf16_kernel(const float* __restrict__ X, size_t count, uint16_t* __restrict__ out,
+                                            unsigned* emax_bits) {
+  float e = 0.0f;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    const float x = __ldg(X + i);
+    const __nv_bfloat16 b = __float2bfloat16_rn(x);
+    const uint16_t bits = __bfloat16_as_ushort(b);
+    out[i] = bits;
+    const float d = fabsf(__uint_as_float((uint32_t)bits << 16) - x);
+    if (isfinite(x)) e = fmaxf(e, d);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(emax_bits, __float_as_uint(e));
+}
+
+// FP8 e4m3 copy, one warp per row: s = max|x| / 448 (1 for a zero row),
+// value = e4m3(x / s) rounded to nearest even and saturated at 448; the
+// dequantised value is s * value in FP32.
+static __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t n, int m, uint8_t* __restrict__ out,
+                                           float* __restrict__ scale, unsigned* emax_bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  float e = 0.0f;
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < n; r += warps) {
+    const float* xr = X + (size_t)r * m;
+    float mx = 0.0f;
+    for (int j = lane; j < m; j += 32) mx = fmaxf(mx, fabsf(__ldg(xr + j)));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float s = mx > 0.0f ? mx / 448.0f : 1.0f;
+    if (lane == 0) scale[r] = s;
+    for (int j = lane; j < m; j += 32) {
+      const float x = __ldg(xr + j);
+      const __nv_fp8_storage_t v = __nv_cvt_float_to_fp8(x / s, __NV_SATFINITE, __NV_E4M3);
+      out[(size_t)r * m + j] = v;
+      __nv_fp8_e4m3 f;
+      f.__x = v;
+      const float d = fabsf(s * static_cast<float>(f) - x);
+      if (isfinite(x)) e = fmaxf(e, d);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (lane == 0) atomicMax(emax_bits, __float_as_uint(e));
+}
+
+}  // namespace knn
+
+using namespace knn;
+
+extern "C" knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, int32_t copies, void* stream_,
+                                         knn_dataset** out) {
+  clear_error();
+  if (!out || !X) return set_error("knn_dataset_create: null pointer"), KNN_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t)1 << 31 || m < 1 || m > kMaxM)
+    return set_error("knn_dataset_create: need 1 <= n < 2^31 and 1 <= m <= 16384"), KNN_EINVAL;
+  if (copies & ~((1 << KNN_STORE_BF16) | (1 << KNN_STORE_FP8)))
+    return set_error("knn_dataset_create: copies must be a mask of BF16 and FP8"), KNN_EINVAL;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  knn_dataset* ds = new knn_dataset();
+  ds->X = X;
+  ds->n = n;
+  ds->m = m;
+  ds->copies = copies;
+  knn_status s = cuda_check(cudaGetDevice(&ds->device), "cudaGetDevice");
+  const size_t count = (size_t)n * (size_t)m;
+  if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->range, 3 * sizeof(uint32_t)), "cudaMalloc(range)");
+  if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->emax, 3 * sizeof(unsigned)), "cudaMalloc(emax)");
+  if (s == KNN_OK && (copies & (1 << KNN_STORE_BF16)))
+    s = cuda_check(cudaMalloc(&ds->xb, count * sizeof(uint16_t)), "cudaMalloc(bf16 copy)");
+  if (s == KNN_OK && (copies & (1 << KNN_STORE_FP8))) {
+    s = cuda_check(cudaMalloc(&ds->x8, count), "cudaMalloc(fp8 copy)");
+    if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->scale8, (size_t)n * sizeof(float)), "cudaMalloc(fp8 scale)");
+  }
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->range, 0xFF, 4, stream), "memset");
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->range + 1, 0x00, 8, stream), "memset");
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->emax, 0x00, 12, stream), "memset");
+  DeviceInfo di;
+  if (s == KNN_OK) s = device_info(&di);
+  if (s == KNN_OK) {
+    const int blocks = (int)std::max<size_t>(1, std::min<size_t>((count + 255) / 256, (size_t)di.sms * 8));
+    minmax_kernel<<<blocks, 256, 0, stream>>>(X, count, ds->range);
+    if (ds->xb) quantize_bf16_kernel<<<blocks, 256, 0, stream>>>(X, count, ds->xb, ds->emax + KNN_STORE_BF16);
+    if (ds->x8)
+      quantize_fp8_kernel<<<di.sms * 8, 256, 0, stream>>>(X, n, m, ds->x8, ds->scale8, ds->emax + KNN_STORE_FP8);
+    s = cuda_check(cudaGetLastError(), "dataset kernels launch");
+  }
+  if (s == KNN_OK) s = cuda_check(cudaStreamSynchronize(stream), "dataset build");
+  if (s == KNN_OK) {
+    unsigned bits[3];
+    s = cuda_check(cudaMemcpy(bits, ds->emax, sizeof(bits), cudaMemcpyDeviceToHost), "read copy errors");
+    for (int i = 0; i < 3 && s == KNN_OK; ++i) memcpy(&ds->emax_host[i], &bits[i], 4);
+  }
+  if (s != KNN_OK) {
+    knn_dataset_destroy(ds);
+    return s;
+  }
+  *out = ds;
+  return KNN_OK;
+}
+
+extern "C" knn_status knn_dataset_destroy(knn_dataset* ds) {
+  if (!ds) return KNN_OK;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ds->device);
+  cudaDeviceSynchronize();
+  cudaFree(ds->range);
+  cudaFree(ds->emax);
+  cudaFree(ds->xb);
+  cudaFree(ds->x8);
+  cudaFree(ds->scale8);
+  cudaSetDevice(cur);
+  delete ds;
+  return KNN_OK;
+}
+
+extern "C" knn_status knn_dataset_error(const knn_dataset* ds, int32_t storage, float* out_error) {
+  clear_error();
+  if (!ds || !out_error || storage < 0 || storage > 2)
+    return set_error("knn_dataset_error: bad arguments"), KNN_EINVAL;
+  *out_error = ds->emax_host[storage];
+  return KNN_OK;
+}
+
+template <class E>
+static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k, double delta,
+                                     uint64_t seed, const knn_opts& o, int64_t* out_idx, int32_t* out_count,
+                                     int64_t* out_evals, int32_t* out_rounds, int32_t* log_code, float* log_S,
+                                     void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+  const int64_t n = ds->n;
+  const int32_t m = ds->m;
+  AdaptivePlan p;
+  knn_status s = plan_adaptive<E>(n, m, nq, k, &o, &p);
+  if (s != KNN_OK) return s;
+  Carve measure;
+  const size_t need = carve_adaptive(measure, n, p, nullptr) + 256;
+  Workspace ws;
+  s = ws.acquire(workspace, workspace_bytes, need, stream);
+  if (s != KNN_OK) return s;
+  Carve cv;
+  cv.base = reinterpret_cast<uint8_t*>(((uintptr_t)ws.ptr + 255) & ~uintptr_t(255));
+  AdaptiveCarve c;
+  carve_adaptive(cv, n, p, &c);
+  s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
+  if (s != KNN_OK) {
+    ws.release();
+    return s;
+  }
+  AdaptiveArgs a;
+  const void* G = ds->X;
+  if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
+  if (E::kStorage == KNN_STORE_FP8) G = ds->x8;
+  a.G = G;
+  a.gscale = ds->scale8;
+  a.emax = E::kStorage == KNN_STORE_F32 ? nullptr : reinterpret_cast<const float*>(ds->emax + E::kStorage);
+  a.Q = Q;
+  a.n = n;
+  a.m = m;
+  a.nq = nq;
+  a.k = k;
+  a.h = o.h;
+  a.bound = o.bound;
+  const double dprime = delta / (double)n;
+  a.a_c0 = 0.0f;
+  a.a_c1 = 0.0f;
+  if (o.bound == KNN_BOUND_FOOTNOTE)
+    a.a_c0 = (float)(std::log(1.0 / dprime) + 3.0 * std::log(std::log(1.0 / dprime)));
+  else if (o.bound == KNN_BOUND_LEMMA)
+    a.a_c0 = (float)std::log(125.0 / dprime);
+  else
+    a.a_c1 = (float)((double)n / delta);
+  a.c_alpha = (float)o.c_alpha;
+  a.B0 = o.B0;
+  a.B = o.B;
+  a.grow = o.grow;
+  a.seed = seed;
+  a.qid_base = o.qid_base;
+  a.mask_p = o.mask_p;
+  a.mask_q = o.mask_q;
+  a.xrange = ds->range;
+  a.ws_ids = c.ids;
+  a.ws_S = c.S;
+  a.ws_C = c.C;
+  a.ws_acc_id = c.acc_id;
+  a.ws_acc_d = c.acc_d;
+  a.ws_acc_U = c.acc_U;
+  a.ws_acc_L = c.acc_L;
+  a.acc_cap = p.acc_cap;
+  a.queue = c.queue;
+  a.out_idx = out_idx;
+  a.out_count = out_count;
+  a.out_evals = out_evals;
+  a.out_rounds = out_rounds;
+  a.log_code = log_code;
+  a.log_S = log_code ? log_S : nullptr;
+  constexpr int V = 16 / (int)sizeof(typename E::T);
+  a.vec = (m % V == 0) && (((uintptr_t)G & 15) == 0);
+  adaptive_rounds_kernel<kAdaptiveNT, E><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
+  s = cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
+  ws.release();
+  return s;
+}
+
+extern "C" knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, const float* Q, int32_t nq, int32_t k,
+                                      double delta, uint64_t seed, const knn_opts* opts, int64_t* out_idx,
+                                      int32_t* out_count, int64_t* out_evals, int32_t* out_rounds, int32_t* log_code,
+                                      float* log_S, void* workspace, size_t workspace_bytes, void* stream_) {
+  clear_error();
+  if (!ds) return set_error("knn_adaptive_ds: null dataset"), KNN_EINVAL;
+  const knn_opts o = resolve(opts, k);
+  knn_status s = validate(ds->n, ds->m, nq, k, delta, o);
+  if (s != KNN_OK) return s;
+  if (o.threads != 0 && o.threads != kAdaptiveNT) return set_error("threads must be 0 or 512"), KNN_EINVAL;
+  if (storage < 0 || storage > 2) return set_error("unknown storage"), KNN_EINVAL;
+  if ((storage == KNN_STORE_BF16 && !ds->xb) || (storage == KNN_STORE_FP8 && !ds->x8))
+    return set_error("knn_adaptive_ds: the dataset was created without that copy"), KNN_EINVAL;
+  if (nq == 0) return KNN_OK;
+  if (!Q || !out_idx || !out_count || !out_evals)
+    return set_error("Q, out_idx, out_count and out_evals are required"), KNN_EINVAL;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (storage == KNN_STORE_BF16)
+    return adaptive_ds_launch<ElemBF16>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
+                                        log_code, log_S, workspace, workspace_bytes, stream);
+  if (storage == KNN_STORE_FP8)
+    return adaptive_ds_launch<ElemFP8>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
+                                       log_code, log_S, workspace, workspace_bytes, stream);
+  return adaptive_ds_launch<ElemF32>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
+                                     log_code, log_S, workspace, workspace_bytes, stream);
+}

@@ -21,6 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 BOUNDS = {"footnote": 0, "lemma": 1, "exp": 2}
+STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
 ACTIVE, ELIMINATED, ACCEPTED = 0, 1, 2
 FULL_MASK = (1 << 64) - 1
 
@@ -44,6 +45,11 @@ _SIGS = {
     "knn_rerank": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P]),
     "knn_exact_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, C.c_int32, C.c_int32]),
     "knn_exact": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
+    "knn_dataset_create": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, _P, C.POINTER(C.c_void_p)]),
+    "knn_dataset_destroy": (C.c_int, [_P]),
+    "knn_dataset_error": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float)]),
+    "knn_adaptive_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
+                                  C.POINTER(Opts), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "knn_last_error": (C.c_char_p, []),
     "knn_version": (C.c_char_p, []),
 }
@@ -138,6 +144,77 @@ def adaptive(X: torch.Tensor, Q: torch.Tensor, k: int, delta: float = 0.01, seed
                             _dev(out["S"], "S") if trace else None, ws_ptr, ws_bytes, _stream(stream))
     _check(rc)
     return out
+
+
+def _alloc_out(nq, n, kh, dev, trace):
+    out = {"idx": torch.empty((nq, kh), dtype=torch.int64, device=dev),
+           "count": torch.empty(nq, dtype=torch.int32, device=dev),
+           "evals": torch.empty(nq, dtype=torch.int64, device=dev),
+           "rounds": torch.empty(nq, dtype=torch.int32, device=dev)}
+    if trace:
+        out["code"] = torch.empty((nq, n), dtype=torch.int32, device=dev)
+        out["S"] = torch.empty((nq, n), dtype=torch.float32, device=dev)
+    return out
+
+
+class Dataset:
+    """A resident dataset (knn_dataset_create): the data range and, on
+    request, BF16 / FP8 copies. X must stay alive and unchanged while the
+    dataset is used; the object keeps a reference to it."""
+
+    def __init__(self, X: torch.Tensor, copies=("bf16", "fp8"), stream=None):
+        mask = 0
+        for c in copies:
+            mask |= 1 << STORAGE[c]
+        self.X = X
+        self.n, self.m = X.shape
+        self.copies = tuple(copies)
+        h = C.c_void_p()
+        _check(lib().knn_dataset_create(_dev(X, "X"), self.n, self.m, mask, _stream(stream), C.byref(h)))
+        self._h = h
+
+    def error(self, storage: str) -> float:
+        """Largest |copy - X| of a copy (0 for f32)."""
+        v = C.c_float()
+        _check(lib().knn_dataset_error(self._h, STORAGE[storage], C.byref(v)))
+        return float(v.value)
+
+    def adaptive(self, Q: torch.Tensor, k: int, delta: float = 0.01, seed: int = 0, *, storage: str = "f32",
+                 trace: bool = False, workspace: torch.Tensor | None = None, stream=None, out=None, **opt_kw):
+        """knn_adaptive_ds: the adaptive rounds gathering from the chosen copy."""
+        nq = Q.shape[0]
+        o = make_opts(k, **opt_kw)
+        h = k if o.h < 0 else o.h
+        if out is None or (trace and "code" not in out):
+            out = _alloc_out(nq, self.n, k + h, Q.device, trace)
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr, ws_bytes = _dev(workspace, "workspace", torch.uint8), workspace.numel()
+        rc = lib().knn_adaptive_ds(self._h, STORAGE[storage], _dev(Q, "Q"), nq, int(k), float(delta), int(seed),
+                                   C.byref(o), _dev(out["idx"], "idx", torch.int64),
+                                   _dev(out["count"], "count", torch.int32), _dev(out["evals"], "evals", torch.int64),
+                                   _dev(out["rounds"], "rounds", torch.int32),
+                                   _dev(out["code"], "code", torch.int32) if trace else None,
+                                   _dev(out["S"], "S") if trace else None, ws_ptr, ws_bytes, _stream(stream))
+        _check(rc)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().knn_dataset_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def rerank(X: torch.Tensor, Q: torch.Tensor, cand: torch.Tensor, k: int, stream=None):
