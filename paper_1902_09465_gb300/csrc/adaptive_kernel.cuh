@@ -69,7 +69,9 @@ struct AdaptiveArgs {
 
 // Element access of the gathered copy. A stored BF16 value is the top half of
 // the FP32 word; an FP8 e4m3 value is converted exactly and multiplied by its
-// row's scale in FP32 (the dequantised value the bounds are built for).
+// row's scale with one FP32 rounding (__fmul_rn, never fused into the
+// following subtraction): fl32(s * value) is the dequantised value the error
+// bound is measured on.
 __device__ __forceinline__ uint32_t word_of(const uint4& r, int i) {
   return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
 }
@@ -210,7 +212,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, int q, int
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
           if (ok[w]) {
-            const float d = (E::kScaled ? xv[w] * sc : xv[w]) - qs[jj[w]];
+            const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
             part = fmaf(d, d, part);
           }
         }
@@ -258,7 +260,7 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
 #pragma unroll
         for (int t = 0; t < V; ++t) {
           const float x = E::lane_of(raw, t);
-          const float d = (E::kScaled ? x * sc : x) - qs[j + t];
+          const float d = (E::kScaled ? __fmul_rn(x, sc) : x) - qs[j + t];
           part = fmaf(d, d, part);
         }
       }
@@ -266,7 +268,7 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
 #pragma unroll 4
       for (int j = lane; j < m; j += 32) {
         const float x = E::load(xr + j);
-        const float d = (E::kScaled ? x * sc : x) - qs[j];
+        const float d = (E::kScaled ? __fmul_rn(x, sc) : x) - qs[j];
         part = fmaf(d, d, part);
       }
     }

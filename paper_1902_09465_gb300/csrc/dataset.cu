@@ -63,7 +63,9 @@ static __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t 
       out[(size_t)r * m + j] = v;
       __nv_fp8_e4m3 f;
       f.__x = v;
-      const float d = fabsf(s * static_cast<float>(f) - x);
+      // the dequantised value is fl32(s * value): __fmul_rn keeps it from
+      // being fused into the subtraction
+      const float d = fabsf(__fmul_rn(s, static_cast<float>(f)) - x);
       if (isfinite(x)) e = fmaxf(e, d);
     }
   }
