@@ -152,9 +152,10 @@ knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const floa
  * request, BF16 and FP8 copies with their largest element error e.
  * (Mixed-precision storage is not in the paper; it cuts gather bytes. The
  * bounds stay valid: a sample of a copy differs from the data's sample by at
- * most eps = e (2 span + e), so the interval width becomes
- * (span + 2e)^2 alpha(T) + eps, and an exact round of a copy keeps width eps.
- * The returned candidates are then reranked on the FP32 data.)
+ * most eps = e (2 span + e), so the width of a sampled interval becomes
+ * (span + 2e)^2 alpha(T) + eps. The exact cap always reads the FP32 data, so
+ * exact distances stay exact (width 0). The returned candidates are then
+ * reranked on the FP32 data.)
  *
  * knn_dataset_create: X is the caller's n x m FP32 device matrix and must
  *   stay alive and unchanged while the dataset is used (FP32 rounds and

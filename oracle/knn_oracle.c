@@ -274,8 +274,8 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
     /* A stored copy moves each sample by at most
      * |xt - x| |xt + x - 2q| <= emax (2 span + emax), so its distances lie
      * within eps of the true ones, and its samples within [0, (span + 2 emax)^2]:
-     * the width of the bound grows accordingly, and an exact round of the
-     * copy still carries eps. */
+     * the width of the sampled bounds grows accordingly. The exact cap reads
+     * the FP32 data, so exact distances keep width 0. */
     const double spanw = span + 2.0 * emax;
     const double span2 = spanw * spanw;
     const double eps = emax * (2.0 * span + emax);
@@ -307,8 +307,8 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
         for (int64_t i = 0; i < n; ++i) {
             if (status[i] != ORC_ACTIVE) continue;
             const float* xi = G + (size_t)i * (size_t)m;
-            if (exact) {
-                Sx[i] = sqdist(xi, q, m);
+            if (exact) { /* the exact distance is taken on the FP32 data itself */
+                Sx[i] = sqdist(X + (size_t)i * (size_t)m, q, m);
             } else {
                 for (int64_t t = Tcur; t < Tn; ++t) {
                     int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, m, p->mask_p, p->mask_q);
@@ -319,7 +319,7 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
             Tx[i] = (int32_t)Tn;
         }
         evals += nact * (exact ? (int64_t)m : Br);
-        const double w = (exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta)) + eps;
+        const double w = exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta) + eps;
 
         /* Bounds of the non-eliminated points: current ones for active
          * points, frozen ones for accepted points. */

@@ -86,6 +86,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   }
 
   AdaptiveArgs a;
+  a.X = X;
   a.G = X;
   a.gscale = nullptr;
   a.emax = nullptr;
@@ -232,6 +233,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
     if (s != KNN_OK) return s;
   }
   AdaptiveArgs a;
+  a.X = X;
   a.G = X;
   a.gscale = nullptr;
   a.emax = nullptr;

@@ -36,6 +36,7 @@
 namespace knn {
 
 struct AdaptiveArgs {
+  const float* X;       // the FP32 data, row-major n x m (exact rounds read it)
   const void* G;        // gathered copy: float, bf16 bits or e4m3 bytes, row-major n x m
   const float* gscale;  // per-row scale of an FP8 copy (else unused)
   const float* emax;    // largest |copy - data| of a stored copy (device scalar; null for FP32)
@@ -64,7 +65,7 @@ struct AdaptiveArgs {
   int32_t* out_rounds;
   int32_t* log_code;
   float* log_S;
-  int32_t vec;  // rows start on 16-byte boundaries: exact rows use 16-byte loads
+  int32_t vec;  // rows of X start on 16-byte boundaries: exact rows use 16-byte loads
 };
 
 // Element access of the gathered copy. A stored BF16 value is the top half of
@@ -72,18 +73,12 @@ struct AdaptiveArgs {
 // row's scale with one FP32 rounding (__fmul_rn, never fused into the
 // following subtraction): fl32(s * value) is the dequantised value the error
 // bound is measured on.
-__device__ __forceinline__ uint32_t word_of(const uint4& r, int i) {
-  return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
-}
-
 struct ElemF32 {
   using T = float;
   static constexpr int kStorage = KNN_STORE_F32;
   static constexpr bool kScaled = false;
   __device__ static __forceinline__ float load(const T* p) { return __ldg(p); }
   __device__ static __forceinline__ float conv(T v) { return v; }
-  // element t of a 16-byte vector (t a compile-time constant after unrolling)
-  __device__ static __forceinline__ float lane_of(const uint4& r, int t) { return __uint_as_float(word_of(r, t)); }
 };
 struct ElemBF16 {
   using T = uint16_t;
@@ -91,9 +86,6 @@ struct ElemBF16 {
   static constexpr bool kScaled = false;
   __device__ static __forceinline__ float conv(T v) { return __uint_as_float((uint32_t)v << 16); }
   __device__ static __forceinline__ float load(const T* p) { return conv(__ldg(p)); }
-  __device__ static __forceinline__ float lane_of(const uint4& r, int t) {
-    return conv((T)(word_of(r, t >> 1) >> (16 * (t & 1))));
-  }
 };
 struct ElemFP8 {
   using T = uint8_t;
@@ -105,9 +97,6 @@ struct ElemFP8 {
     return static_cast<float>(f);
   }
   __device__ static __forceinline__ float load(const T* p) { return conv(__ldg(p)); }
-  __device__ static __forceinline__ float lane_of(const uint4& r, int t) {
-    return conv((T)(word_of(r, t >> 2) >> (8 * (t & 3))));
-  }
 };
 
 constexpr int kIPT = 4;  // consecutive slots per thread in the decide pass
@@ -239,36 +228,35 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, int q, int
   }
 }
 
-// Exact round: one warp per active point, the full row (16-byte loads when
-// rows are 16-byte aligned).
-template <int NT, class E>
+// Exact round: one warp per active point, the full FP32 row of the data
+// (16-byte loads when rows are 16-byte aligned).
+template <int NT>
 __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int nact, const float* qs,
                                              const int32_t* idc, float* Sc, uint32_t* hist) {
-  using T = typename E::T;
-  constexpr int V = 16 / sizeof(T);  // elements per 16-byte load
   const int m = a.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int sidx = warp; sidx < nact; sidx += NT / 32) {
     const int id = (r == 0) ? sidx : idc[sidx];
-    const T* xr = static_cast<const T*>(a.G) + (size_t)id * (size_t)m;
-    const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
+    const float* xr = a.X + (size_t)id * (size_t)m;
     float part = 0.0f;
     if (a.vec) {
-#pragma unroll 2
-      for (int j = lane * V; j < m; j += 32 * V) {
-        const uint4 raw = __ldg(reinterpret_cast<const uint4*>(xr + j));
-#pragma unroll
-        for (int t = 0; t < V; ++t) {
-          const float x = E::lane_of(raw, t);
-          const float d = (E::kScaled ? __fmul_rn(x, sc) : x) - qs[j + t];
-          part = fmaf(d, d, part);
-        }
+#pragma unroll 4
+      for (int j = lane * 4; j < m; j += 128) {
+        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr + j));
+        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+        float d = x4.x - q4.x;
+        part = fmaf(d, d, part);
+        d = x4.y - q4.y;
+        part = fmaf(d, d, part);
+        d = x4.z - q4.z;
+        part = fmaf(d, d, part);
+        d = x4.w - q4.w;
+        part = fmaf(d, d, part);
       }
     } else {
 #pragma unroll 4
       for (int j = lane; j < m; j += 32) {
-        const float x = E::load(xr + j);
-        const float d = (E::kScaled ? __fmul_rn(x, sc) : x) - qs[j];
+        const float d = __ldg(xr + j) - qs[j];
         part = fmaf(d, d, part);
       }
     }
@@ -338,8 +326,8 @@ __global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) 
     const float span = fmaxf(xmax, qmax) - fminf(xmin, qmin);
     // A stored copy moves each sample by at most e (2 span + e), e its largest
     // element error: the copy's samples lie in [0, (span + 2e)^2] and its
-    // distances within eps of the data's, so the width grows by eps (also in
-    // the exact round of the copy).
+    // distances within eps of the data's, so the width of sampled bounds
+    // grows by eps. Exact rounds read the FP32 data and keep width 0.
     float spanw = span, eps = 0.0f;
     if (E::kStorage != KNN_STORE_F32) {
       const float e = *a.emax;
@@ -385,13 +373,13 @@ __global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) 
       float* Cc = C0 + (size_t)cur * n;
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
-      if (exact)
-        gather_exact<NT, E>(a, r, nact, qs, idc, Sc, hist);
+      if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
+        gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
       else
         gather_sampled<NT, E>(a, q, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
       __syncthreads();
       evals += (int64_t)nact * (exact ? (int64_t)m : Br);
-      const float w = (exact ? 0.0f : span2 * alpha_of(a, Tn)) + eps;
+      const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
       const float Tf = (float)Tn;
 
       // ---- thresholds

@@ -182,6 +182,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
   if (E::kStorage == KNN_STORE_FP8) G = ds->x8;
+  a.X = ds->X;
   a.G = G;
   a.gscale = ds->scale8;
   a.emax = E::kStorage == KNN_STORE_F32 ? nullptr : reinterpret_cast<const float*>(ds->emax + E::kStorage);
@@ -225,8 +226,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.out_rounds = out_rounds;
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
-  constexpr int V = 16 / (int)sizeof(typename E::T);
-  a.vec = (m % V == 0) && (((uintptr_t)G & 15) == 0);
+  a.vec = (m % 4 == 0) && (((uintptr_t)ds->X & 15) == 0);
   adaptive_rounds_kernel<kAdaptiveNT, E><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
   s = cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
   ws.release();
