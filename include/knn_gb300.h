@@ -159,8 +159,9 @@ knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const floa
  *
  * knn_dataset_create: X is the caller's n x m FP32 device matrix and must
  *   stay alive and unchanged while the dataset is used (FP32 rounds and
- *   reranks read it). `copies` is a bit mask of (1 << KNN_STORE_BF16) and
- *   (1 << KNN_STORE_FP8). Allocates the copies with cudaMalloc, builds them
+ *   reranks read it). `copies` is a bit mask of (1 << KNN_STORE_BF16),
+ *   (1 << KNN_STORE_FP8) and KNN_COPY_SCREEN (the operand of the
+ *   tensor-core screen of knn_exact_ds). Allocates the copies with cudaMalloc, builds them
  *   on `stream` and waits for them. *out receives the handle.
  * knn_dataset_destroy: frees the copies (waits for the device first).
  * knn_dataset_error: largest |copy - X| of a copy (host value; 0 for F32).
@@ -168,6 +169,7 @@ knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const floa
  *   copy (same outputs, same workspace size as knn_adaptive).
  */
 typedef struct knn_dataset knn_dataset;
+enum { KNN_COPY_SCREEN = 1 << 3 };
 knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, int32_t copies, void* stream,
                               knn_dataset** out);
 knn_status knn_dataset_destroy(knn_dataset* ds);
@@ -205,6 +207,28 @@ size_t knn_exact_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k);
 knn_status knn_exact(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
                      int64_t* out_idx, double* out_dist,
                      void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * knn_exact_ds -- the naive exact method over a resident dataset, with a
+ * choice of screen:
+ *   KNN_SCREEN_F32     the FP32 SIMT screen of knn_exact;
+ *   KNN_SCREEN_BF16X3  a tcgen05 tensor-core GEMM on the centred data split
+ *                      into BF16 hi + lo parts (three products per pair,
+ *                      FP32 accumulation in tensor memory); needs a dataset
+ *                      created with KNN_COPY_SCREEN and an sm_10x device.
+ * Both keep every point within twice the screen's proven error bound of the
+ * k-th screened value and rerank those in FP64 (knn_rerank), so the result
+ * is exact: the k nearest by (distance, index).
+ */
+enum { KNN_SCREEN_F32 = 0, KNN_SCREEN_BF16X3 = 1 };
+size_t knn_exact_ds_workspace_size(const knn_dataset* ds, int32_t screen, int32_t nq);
+knn_status knn_exact_ds(const knn_dataset* ds, int32_t screen, const float* Q, int32_t nq, int32_t k,
+                        int64_t* out_idx, double* out_dist, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Library status of the current device: 0, or a nonzero code recorded by a
+ * kernel that gave up a bounded wait (the call's outputs are then invalid).
+ * Waits for the device, then clears the status. */
+knn_status knn_device_status(int32_t* out);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* knn_last_error(void);

@@ -75,7 +75,44 @@ void Workspace::release() {
   owned = false;
 }
 
+// Status word per device (see knn_device_status).
+static __device__ int g_device_status;
+
+knn_status device_status_ptr(int** out) {
+  static std::mutex mu;
+  static int* addr[64] = {};
+  int dev = 0;
+  knn_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (s != KNN_OK) return s;
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range");
+    return KNN_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    s = cuda_check(cudaGetSymbolAddress(&p, g_device_status), "cudaGetSymbolAddress(status)");
+    if (s != KNN_OK) return s;
+    addr[dev] = static_cast<int*>(p);
+  }
+  *out = addr[dev];
+  return KNN_OK;
+}
+
 }  // namespace knn
+
+extern "C" knn_status knn_device_status(int32_t* out) {
+  knn::clear_error();
+  if (!out) return knn::set_error("knn_device_status: null pointer"), KNN_EINVAL;
+  int* p = nullptr;
+  knn_status s = knn::device_status_ptr(&p);
+  if (s != KNN_OK) return s;
+  int v = 0;
+  s = knn::cuda_check(cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  if (s == KNN_OK && v != 0) s = knn::cuda_check(cudaMemset(p, 0, sizeof(int)), "clear status");
+  *out = v;
+  return s;
+}
 
 extern "C" const char* knn_last_error(void) { return knn::g_last_error.c_str(); }
 

@@ -7,21 +7,9 @@
 
 #include "adaptive_kernel.cuh"
 
-struct knn_dataset {
-  const float* X = nullptr;
-  int64_t n = 0;
-  int32_t m = 0;
-  int32_t copies = 0;
-  int device = 0;
-  uint32_t* range = nullptr;  // [3]: min key, max key (finite values), non-finite flag
-  uint16_t* xb = nullptr;     // BF16 copy
-  uint8_t* x8 = nullptr;      // FP8 e4m3 copy
-  float* scale8 = nullptr;    // FP8 per-row scale
-  unsigned* emax = nullptr;   // [3]: largest |copy - X| per storage, as float bits
-  float emax_host[3] = {0.0f, 0.0f, 0.0f};
-};
-
 namespace knn {
+
+knn_status build_screen_operand(knn_dataset* ds, cudaStream_t stream);
 
 // BF16 copy (round to nearest even) and its largest element error.
 static __global__ void quantize_bf16_kernel(const float* __restrict__ X, size_t count, uint16_t* __restrict__ out,
@@ -85,8 +73,8 @@ extern "C" knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, i
   *out = nullptr;
   if (n < 1 || n >= (int64_t)1 << 31 || m < 1 || m > kMaxM)
     return set_error("knn_dataset_create: need 1 <= n < 2^31 and 1 <= m <= 16384"), KNN_EINVAL;
-  if (copies & ~((1 << KNN_STORE_BF16) | (1 << KNN_STORE_FP8)))
-    return set_error("knn_dataset_create: copies must be a mask of BF16 and FP8"), KNN_EINVAL;
+  if (copies & ~((1 << KNN_STORE_BF16) | (1 << KNN_STORE_FP8) | KNN_COPY_SCREEN))
+    return set_error("knn_dataset_create: copies must be a mask of BF16, FP8 and the screen operand"), KNN_EINVAL;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   knn_dataset* ds = new knn_dataset();
   ds->X = X;
@@ -116,6 +104,7 @@ extern "C" knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, i
       quantize_fp8_kernel<<<di.sms * 8, 256, 0, stream>>>(X, n, m, ds->x8, ds->scale8, ds->emax + KNN_STORE_FP8);
     s = cuda_check(cudaGetLastError(), "dataset kernels launch");
   }
+  if (s == KNN_OK && (copies & KNN_COPY_SCREEN)) s = build_screen_operand(ds, stream);
   if (s == KNN_OK) s = cuda_check(cudaStreamSynchronize(stream), "dataset build");
   if (s == KNN_OK) {
     unsigned bits[3];
@@ -141,6 +130,10 @@ extern "C" knn_status knn_dataset_destroy(knn_dataset* ds) {
   cudaFree(ds->xb);
   cudaFree(ds->x8);
   cudaFree(ds->scale8);
+  cudaFree(ds->screenA);
+  cudaFree(ds->mu);
+  cudaFree(ds->xcn);
+  cudaFree(ds->xcn_max);
   cudaSetDevice(cur);
   delete ds;
   return KNN_OK;

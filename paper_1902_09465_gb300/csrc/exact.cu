@@ -18,6 +18,9 @@ namespace knn {
 
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream);
+size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq);
+knn_status exact_tc(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k, int64_t* out_idx,
+                    double* out_dist, void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 constexpr int kExactCand = 2048;  // candidate slots per query before falling back to a full scan
 
@@ -131,12 +134,16 @@ __global__ void __launch_bounds__(256) screen_sgemm_kernel(const float* __restri
 
 // Per query: k-th smallest screened value, then every point within 2 E_q of
 // it into cand[q, 0..kExactCand) (-1 padded); a row that does not fit is
-// marked -2 (rerank then scans every point).
+// marked -2 (rerank then scans every point). E_q is the screen's error bound
+// for the query: c_cross ||x||max ||q|| + c_square (||x||max + ||q||)^2,
+// with the norms of the vectors the screen multiplied (FP32 sums, inflated by
+// their own rounding bound).
 constexpr int kSelNT = 512;
 
 __global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __restrict__ D, int64_t n, int m, int k,
                                                                const float* __restrict__ qn,
                                                                const unsigned* __restrict__ xn_max_bits,
+                                                               float c_cross, float c_square,
                                                                int64_t* __restrict__ cand) {
   __shared__ uint32_t hist[kHistBins];
   __shared__ uint32_t buf[kSelCap];
@@ -151,17 +158,14 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __re
   __syncthreads();
   select_smallest<kSelNT>([&](int i) { return f2key(__ldg(dr + i)); }, (int)n, k, hist, buf, ss, bs);
   const float tau = key2f(buf[k - 1]);
-  // Rounding bound of the screen (unit roundoff u = 2^-24): the dot product
-  // and the two norms are length-m FP32 sums (error <= gamma_m times the
-  // sum of magnitudes, gamma_m = m u / (1 - m u)), plus two final roundings;
-  // all magnitudes are bounded by (||x|| + ||q||)^2. The norms themselves
-  // carry relative error gamma_m; a factor 2 covers the second-order terms.
-  const double u = 1.0 / 16777216.0;
-  const double gm = (double)(m + 2) * u / (1.0 - (double)(m + 2) * u);
-  const double xmax = sqrt((double)__uint_as_float(*xn_max_bits) * (1.0 + gm));
-  const double qq = sqrt((double)qn[q] * (1.0 + gm));
-  const double E = 2.0 * (gm + 4.0 * u) * (xmax + qq) * (xmax + qq);
-  const float thr = (float)((double)tau + 2.0 * E) * (1.0f + 4.0f / 16777216.0f);
+  // FP32 arithmetic on non-negative terms: a few units of roundoff, covered
+  // by the factor 1.001 (the coefficients carry their own margins)
+  const float u = 1.0f / 16777216.0f;
+  const float gm = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);
+  const float xmax = sqrtf(__uint_as_float(*xn_max_bits) * (1.0f + gm));
+  const float qq = sqrtf(qn[q] * (1.0f + gm));
+  const float E = 1.001f * (c_cross * xmax * qq + c_square * (xmax + qq) * (xmax + qq));
+  const float thr = (tau + 2.0f * E) * (1.0f + 4.0f * u);
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   int64_t* cr = cand + (size_t)q * kExactCand;
@@ -178,6 +182,23 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __re
   } else {
     for (int t = c + threadIdx.x; t < kExactCand; t += kSelNT) cr[t] = -1;
   }
+}
+
+knn_status launch_screen_select(const float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
+                                const unsigned* xn_max_bits, double c_cross, double c_square, int64_t* cand,
+                                cudaStream_t stream) {
+  screen_select_kernel<<<nq, kSelNT, 0, stream>>>(D, n, m, k, qn, xn_max_bits, (float)c_cross, (float)c_square,
+                                                  cand);
+  return cuda_check(cudaGetLastError(), "screen_select_kernel launch");
+}
+
+// SIMT screen bound: the dot product and both norms are length-m FP32 sums
+// (gamma_m times the sum of magnitudes), plus two final roundings, all
+// bounded by (||x|| + ||q||)^2; a factor 2 covers second-order terms.
+static double simt_c_square(int m) {
+  const double u = 1.0 / 16777216.0;
+  const double gm = (double)(m + 2) * u / (1.0 - (double)(m + 2) * u);
+  return 2.0 * (gm + 4.0 * u);
 }
 
 struct ExactCarve {
@@ -241,10 +262,33 @@ extern "C" knn_status knn_exact(const float* X, int64_t n, int32_t m, const floa
     row_norms_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(Q, nq, m, c.qn, nullptr);
     dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((nq + kBN - 1) / kBN));
     screen_sgemm_kernel<<<grid, 256, 0, stream>>>(X, Q, n, nq, m, c.xn, c.qn, c.D);
-    screen_select_kernel<<<nq, kSelNT, 0, stream>>>(c.D, n, m, k, c.qn, c.xmax, c.cand);
     s = cuda_check(cudaGetLastError(), "exact kernels launch");
+    if (s == KNN_OK) s = launch_screen_select(c.D, n, nq, m, k, c.qn, c.xmax, 0.0, simt_c_square(m), c.cand, stream);
   }
   if (s == KNN_OK) s = launch_rerank(X, n, m, Q, nq, c.cand, kExactCand, k, out_idx, out_dist, stream);
   ws.release();
   return s;
+}
+
+extern "C" size_t knn_exact_ds_workspace_size(const knn_dataset* ds, int32_t screen, int32_t nq) {
+  if (!ds) return 0;
+  if (screen == KNN_SCREEN_BF16X3) return exact_tc_workspace(ds->n, ds->m, nq);
+  return knn_exact_workspace_size(ds->n, ds->m, nq, 1);
+}
+
+extern "C" knn_status knn_exact_ds(const knn_dataset* ds, int32_t screen, const float* Q, int32_t nq, int32_t k,
+                                   int64_t* out_idx, double* out_dist, void* workspace, size_t workspace_bytes,
+                                   void* stream_) {
+  clear_error();
+  if (!ds) return set_error("knn_exact_ds: null dataset"), KNN_EINVAL;
+  if (k < 1 || k > ds->n || k > kMaxKH || nq < 0)
+    return set_error("knn_exact_ds: need 1 <= k <= min(n, 1024), nq >= 0"), KNN_EINVAL;
+  if (screen != KNN_SCREEN_F32 && screen != KNN_SCREEN_BF16X3)
+    return set_error("knn_exact_ds: unknown screen"), KNN_EINVAL;
+  if (nq == 0) return KNN_OK;
+  if (!Q || !out_idx || !out_dist) return set_error("knn_exact_ds: null pointer"), KNN_EINVAL;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (screen == KNN_SCREEN_BF16X3)
+    return exact_tc(ds, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream);
+  return knn_exact(ds->X, ds->n, ds->m, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream_);
 }

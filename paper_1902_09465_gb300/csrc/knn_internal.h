@@ -50,4 +50,29 @@ struct Workspace {
   void release();
 };
 
+// Library status word of the current device: kernels that give up a bounded
+// wait record a code here (read and cleared by knn_device_status).
+knn_status device_status_ptr(int** out);
+
 }  // namespace knn
+
+// A resident dataset (see knn_dataset_create).
+struct knn_dataset {
+  const float* X = nullptr;
+  int64_t n = 0;
+  int32_t m = 0;
+  int32_t copies = 0;
+  int device = 0;
+  uint32_t* range = nullptr;  // [3]: min key, max key (finite values), non-finite flag
+  uint16_t* xb = nullptr;     // BF16 copy
+  uint8_t* x8 = nullptr;      // FP8 e4m3 copy
+  float* scale8 = nullptr;    // FP8 per-row scale
+  unsigned* emax = nullptr;   // [3]: largest |copy - X| per storage, as float bits
+  float emax_host[3] = {0.0f, 0.0f, 0.0f};
+  // tensor-core screen operand: rows [hi | hi | lo] of (x - mu), each part Kp wide
+  int32_t Kp = 0;
+  uint16_t* screenA = nullptr;
+  float* mu = nullptr;        // column means
+  float* xcn = nullptr;       // ||x_i - mu||^2
+  unsigned* xcn_max = nullptr;  // largest of them, float bits
+};

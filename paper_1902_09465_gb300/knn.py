@@ -22,6 +22,8 @@ _lib = None
 
 BOUNDS = {"footnote": 0, "lemma": 1, "exp": 2}
 STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
+COPY_SCREEN = 1 << 3
+SCREENS = {"f32": 0, "bf16x3": 1}
 ACTIVE, ELIMINATED, ACCEPTED = 0, 1, 2
 FULL_MASK = (1 << 64) - 1
 
@@ -50,6 +52,9 @@ _SIGS = {
     "knn_dataset_error": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_float)]),
     "knn_adaptive_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
                                   C.POINTER(Opts), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "knn_exact_ds_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32]),
+    "knn_exact_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
+    "knn_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
     "knn_last_error": (C.c_char_p, []),
     "knn_version": (C.c_char_p, []),
 }
@@ -165,7 +170,7 @@ class Dataset:
     def __init__(self, X: torch.Tensor, copies=("bf16", "fp8"), stream=None):
         mask = 0
         for c in copies:
-            mask |= 1 << STORAGE[c]
+            mask |= COPY_SCREEN if c == "screen" else 1 << STORAGE[c]
         self.X = X
         self.n, self.m = X.shape
         self.copies = tuple(copies)
@@ -198,6 +203,23 @@ class Dataset:
                                    _dev(out["S"], "S") if trace else None, ws_ptr, ws_bytes, _stream(stream))
         _check(rc)
         return out
+
+    def exact_workspace_size(self, nq: int, screen: str = "bf16x3") -> int:
+        return int(lib().knn_exact_ds_workspace_size(self._h, SCREENS[screen], int(nq)))
+
+    def exact(self, Q: torch.Tensor, k: int, screen: str = "bf16x3", workspace: torch.Tensor | None = None,
+              stream=None):
+        """knn_exact_ds: the naive exact method with the chosen screen.
+        Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+        nq = Q.shape[0]
+        idx = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dist = torch.empty((nq, k), dtype=torch.float64, device=Q.device)
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr, ws_bytes = _dev(workspace, "workspace", torch.uint8), workspace.numel()
+        _check(lib().knn_exact_ds(self._h, SCREENS[screen], _dev(Q, "Q"), nq, int(k), _dev(idx, "idx", torch.int64),
+                                  _dev(dist, "dist", torch.float64), ws_ptr, ws_bytes, _stream(stream)))
+        return idx, dist
 
     def close(self):
         if getattr(self, "_h", None):
@@ -247,6 +269,14 @@ def exact(X: torch.Tensor, Q: torch.Tensor, k: int, workspace: torch.Tensor | No
                          _dev(dist, "dist", torch.float64), ws_ptr, ws_bytes, _stream(stream))
     _check(rc)
     return idx, dist
+
+
+def device_status() -> int:
+    """Library status of the current device (waits for the device, clears it):
+    nonzero if a kernel gave up a bounded wait."""
+    v = C.c_int32()
+    _check(lib().knn_device_status(C.byref(v)))
+    return int(v.value)
 
 
 def version() -> str:
