@@ -148,7 +148,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     B0, B, grow = args.B0, args.B, args.grow
 
-    ds = knn.Dataset(Xd, copies=("bf16", "fp8"))
+    ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen"))
 
     def adaptive_step(Qx, c_alpha, qid_base, out=None, storage="f32"):
         res = ds.adaptive(Qx, k, w["delta"], 0, storage=storage, bound="exp", c_alpha=c_alpha, B0=B0, B=B,
@@ -235,24 +235,29 @@ def run_ours(args, rank, world, local_rank):
     sector_gbs = 32 * evals / (kern_ms / 1e3) / 1e9
 
     # ---- recall of the timed batch against the exact method
-    ti, td = knn.exact(Xd, Qd, k)
+    ti, td = ds.exact(Qd, k, screen="f32")
     torch.cuda.synchronize()
     rec = recall_of(ri.cpu().numpy(), rd.cpu().numpy(), ti.cpu().numpy(), td.cpu().numpy())
 
-    # ---- exact baseline on the same batch
-    ex_ws = torch.empty(knn.exact_workspace_size(n, m, nq, k), dtype=torch.uint8, device=dev)
-    for _ in range(2):
-        knn.exact(Xd, Qd, k, workspace=ex_ws)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # ---- exact baseline on the same batch: tensor-core screen (and the FP32 SIMT screen)
+    def time_exact(screen, steps):
+        ws = torch.empty(ds.exact_workspace_size(nq, screen), dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            ds.exact(Qd, k, screen=screen, workspace=ws)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ei, ed = ds.exact(Qd, k, screen=screen, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / steps), ei
+
     ex_steps = max(2, min(args.steps, 5))
-    for _ in range(ex_steps):
-        knn.exact(Xd, Qd, k, workspace=ex_ws)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    exact_ms = max_over_ranks(e0.elapsed_time(e1) / ex_steps)
+    exact_ms, ei_tc = time_exact("bf16x3", ex_steps)
+    exact_simt_ms, _ = time_exact("f32", 2)
+    exact_agree = bool(torch.equal(ei_tc, ti))
 
     # ---- stored copies (BF16, FP8 e4m3 + per-row scale): same step, calibrated separately
     variants = {}
@@ -327,7 +332,10 @@ def run_ours(args, rank, world, local_rank):
         "rounds_mean": round(float(rounds.mean()), 3),
         "storage_variants": variants,
         "exact_baseline": {"queries_per_s": round(world * nq / (exact_ms / 1e3), 3), "ms_per_batch": round(exact_ms, 4),
-                           "method": "FP32 SIMT screen GEMM + select + FP64 rerank (exact)"},
+                           "method": "tcgen05 BF16x3 screen GEMM + select + FP64 rerank (exact)",
+                           "agrees_with_simt_path": exact_agree,
+                           "simt_f32_screen": {"queries_per_s": round(world * nq / (exact_simt_ms / 1e3), 3),
+                                               "ms_per_batch": round(exact_simt_ms, 4)}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 5), "traffic": None,
                      "kernel": "adaptive_rounds_kernel<512, ElemF32>", "kernel_ms": round(kern_ms, 4),
