@@ -9,7 +9,7 @@ generators.
 
 import importlib
 
-__all__ = ["knn", "synth", "build"]
+__all__ = ["knn", "synth", "build", "runtime"]
 
 
 def __getattr__(name):

@@ -40,10 +40,6 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   const knn_opts o = resolve(opts, k);
   knn_status s = validate(n, m, nq, k, delta, o);
   if (s != KNN_OK) return s;
-  if (o.threads != 0 && o.threads != kAdaptiveNT) {
-    set_error("threads must be 0 or 512");
-    return KNN_EINVAL;
-  }
   if (nq == 0) return KNN_OK;
   if (!X || !Q || !out_idx || !out_count || !out_evals) {
     set_error("X, Q, out_idx, out_count and out_evals are required");
@@ -131,8 +127,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
-  adaptive_rounds_kernel<kAdaptiveNT, ElemF32><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
-  s = cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
+  s = launch_rounds<ElemF32>(p, a, stream);
   ws.release();
   return s;
 }
@@ -183,10 +178,6 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   const knn_opts o = resolve(opts, k);
   knn_status s = validate(n, m, nq, k, delta, o);
   if (s != KNN_OK) return s;
-  if (o.threads != 0 && o.threads != kAdaptiveNT) {
-    set_error("threads must be 0 or 512");
-    return KNN_EINVAL;
-  }
   if (nq == 0) return KNN_OK;
   if (!X || !Q || !out_idx || !out_count || !out_evals) {
     set_error("X, Q, out_idx, out_count and out_evals are required");
@@ -278,6 +269,5 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
-  adaptive_rounds_kernel<kAdaptiveNT, ElemF32><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
-  return cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
+  return launch_rounds<ElemF32>(p, a, stream);
 }

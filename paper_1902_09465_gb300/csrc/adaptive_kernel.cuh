@@ -270,7 +270,7 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
 }
 
 template <int NT, class E>
-__global__ void __launch_bounds__(NT, 2) adaptive_rounds_kernel(AdaptiveArgs a) {
+__global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(AdaptiveArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ AdaptiveShared<NT> sh;
   const int m = a.m;
@@ -594,7 +594,7 @@ static __global__ void minmax_kernel(const float* __restrict__ X, size_t count, 
 
 // --------------------------------------------------------------- host side
 
-constexpr int kAdaptiveNT = 512;
+constexpr int kAdaptiveNT = 512;  // default threads per CTA (256 is the other choice)
 
 static size_t adaptive_smem_bytes(int m) {
   const size_t mpad = (size_t)((m + 3) & ~3);
@@ -604,23 +604,32 @@ static size_t adaptive_smem_bytes(int m) {
 
 struct AdaptivePlan {
   int grid = 0;
+  int threads = kAdaptiveNT;
   int acc_cap = 0;
   size_t smem = 0;
 };
+
+// The round-loop kernel instantiated for a thread count (512 or 256; both
+// keep 64 registers per thread, 32 or 16 warps per query).
+template <class E>
+static void* rounds_kernel_for(int threads) {
+  return threads == 256 ? reinterpret_cast<void*>(adaptive_rounds_kernel<256, E>)
+                        : reinterpret_cast<void*>(adaptive_rounds_kernel<512, E>);
+}
 
 template <class E>
 static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* o, AdaptivePlan* p) {
   DeviceInfo di;
   knn_status s = device_info(&di);
   if (s != KNN_OK) return s;
+  p->threads = (o && o->threads == 256) ? 256 : kAdaptiveNT;
   p->smem = adaptive_smem_bytes(m);
-  s = cuda_check(cudaFuncSetAttribute(adaptive_rounds_kernel<kAdaptiveNT, E>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
+  const void* fn = rounds_kernel_for<E>(p->threads);
+  s = cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
                  "cudaFuncSetAttribute(adaptive)");
   if (s != KNN_OK) return s;
   int per_sm = 0;
-  s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adaptive_rounds_kernel<kAdaptiveNT, E>,
-                                                                 kAdaptiveNT, p->smem),
+  s = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, p->threads, p->smem),
                  "occupancy(adaptive)");
   if (s != KNN_OK) return s;
   if (per_sm < 1) {
@@ -635,6 +644,15 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   p->acc_cap = 2 * k + 2;
   (void)n;
   return KNN_OK;
+}
+
+template <class E>
+static knn_status launch_rounds(const AdaptivePlan& p, const AdaptiveArgs& a, cudaStream_t stream) {
+  if (p.threads == 256)
+    adaptive_rounds_kernel<256, E><<<p.grid, 256, p.smem, stream>>>(a);
+  else
+    adaptive_rounds_kernel<512, E><<<p.grid, 512, p.smem, stream>>>(a);
+  return cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
 }
 
 struct AdaptiveCarve {
@@ -678,6 +696,8 @@ static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double d
     return set_error("footnote bound needs delta/n < 1/e"), KNN_EINVAL;
   if (o.bound == KNN_BOUND_EXP && !(o.c_alpha > 0.0)) return set_error("c_alpha must be > 0"), KNN_EINVAL;
   if (o.B0 < 1 || o.B < 1) return set_error("B0 and B must be >= 1"), KNN_EINVAL;
+  if (o.threads != 0 && o.threads != 256 && o.threads != 512)
+    return set_error("threads must be 0, 256 or 512"), KNN_EINVAL;
   if (o.grow != 0 && o.grow != 1) return set_error("grow must be 0 or 1"), KNN_EINVAL;
   return KNN_OK;
 }

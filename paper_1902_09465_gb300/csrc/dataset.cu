@@ -220,8 +220,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)ds->X & 15) == 0);
-  adaptive_rounds_kernel<kAdaptiveNT, E><<<p.grid, kAdaptiveNT, p.smem, stream>>>(a);
-  s = cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
+  s = launch_rounds<E>(p, a, stream);
   ws.release();
   return s;
 }
@@ -235,7 +234,6 @@ extern "C" knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, co
   const knn_opts o = resolve(opts, k);
   knn_status s = validate(ds->n, ds->m, nq, k, delta, o);
   if (s != KNN_OK) return s;
-  if (o.threads != 0 && o.threads != kAdaptiveNT) return set_error("threads must be 0 or 512"), KNN_EINVAL;
   if (storage < 0 || storage > 2) return set_error("unknown storage"), KNN_EINVAL;
   if ((storage == KNN_STORE_BF16 && !ds->xb) || (storage == KNN_STORE_FP8 && !ds->x8))
     return set_error("knn_adaptive_ds: the dataset was created without that copy"), KNN_EINVAL;

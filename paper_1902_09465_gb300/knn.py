@@ -98,7 +98,7 @@ def _stream(stream):
 
 
 def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid_base=0, share_points=False,
-              share_queries=False, max_ctas=0) -> Opts:
+              share_queries=False, max_ctas=0, threads=0) -> Opts:
     o = Opts()
     lib().knn_opts_default(C.byref(o))
     o.h = -1 if h is None else int(h)
@@ -109,6 +109,7 @@ def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid
     o.mask_p = 0 if share_points else FULL_MASK
     o.mask_q = 0 if share_queries else FULL_MASK
     o.max_ctas = int(max_ctas)
+    o.threads = int(threads)
     return o
 
 

@@ -1,0 +1,63 @@
+"""Batched execution: CUDA-graph replay of the adaptive step, the thread-count
+variant of the round-loop kernel, and the autotuner."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1902_09465_gb300 import knn, runtime, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def data():
+    X, Q = synth.pixel_mixture(30000, 256, 160, seed=21)
+    Xd = torch.from_numpy(X).cuda()
+    ds = knn.Dataset(Xd, copies=("bf16",))
+    yield ds, torch.from_numpy(Q).cuda()
+    ds.close()
+
+
+def test_threads_256_and_512_give_identical_results(data):
+    ds, Qd = data
+    a = ds.adaptive(Qd, 10, 0.01, 3, bound="exp", c_alpha=1e-3, grow=1, threads=512, trace=True)
+    b = ds.adaptive(Qd, 10, 0.01, 3, bound="exp", c_alpha=1e-3, grow=1, threads=256, trace=True)
+    for key in a:
+        assert torch.equal(a[key], b[key]), key
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_graph_replay_matches_eager(data, storage):
+    ds, Qd = data
+    step = runtime.GraphStep(ds, 64, 10, 0.01, 5, storage=storage, bound="exp", c_alpha=1e-3, grow=1)
+    for part in (Qd[:64], Qd[64:128], Qd[:64]):
+        res, ri, rd = step.run(part)
+        torch.cuda.synchronize()
+        e = ds.adaptive(part.contiguous(), 10, 0.01, 5, storage=storage, bound="exp", c_alpha=1e-3, grow=1)
+        ei, ed = knn.rerank(ds.X, part.contiguous(), e["idx"], 10)
+        for key in ("idx", "count", "evals", "rounds"):
+            assert torch.equal(res[key], e[key]), key
+        assert torch.equal(ri, ei) and torch.equal(rd, ed)
+
+
+def test_autotune_picks_a_configuration_meeting_the_target(data, tmp_path):
+    ds, Qd = data
+    cache = str(tmp_path / "tune.json")
+    H = Qd[96:160].contiguous()
+    out = runtime.autotune(ds, H, 10, 0.01, schedules=((16, 16, 1), (8, 8, 0)), threads=(512, 256),
+                           c_grid=(1e-2, 1e-3, 1e-4), cache=cache)
+    best = out["best"]
+    assert best in out["table"] and best["queries_per_s"] == max(r["queries_per_s"] for r in out["table"])
+    res = ds.adaptive(H, 10, 0.01, 0, bound="exp", c_alpha=best["c_alpha"], B0=best["B0"], B=best["B"],
+                      grow=best["grow"], threads=best["threads"], qid_base=1 << 41)
+    ri, rd = knn.rerank(ds.X, H, res["idx"], 10)
+    ti, td = ds.exact(H, 10, screen="f32")
+    assert runtime.recall(ri, rd, ti, td) >= 0.999
+    with open(cache) as f:
+        assert runtime.tune_key(ds, 10, "f32") in json.load(f)
+    again = runtime.autotune(ds, H, 10, 0.01, cache=cache)   # served from the cache
+    assert again == out
