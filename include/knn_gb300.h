@@ -181,6 +181,24 @@ knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, const float* 
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * knn_adaptive_ds_multi -- one launch over a mixed batch: query q uses its
+ * own k = k_per_query[q] (1 <= k <= k_max) and its own Philox query id
+ * query_ids[q] (both device arrays), so a query's draws, decisions and
+ * result do not depend on which batch or position it runs in. h is
+ * opts->h, or each query's own k when opts->h < 0. out_idx rows are
+ * k_max + h_max long (h_max = opts->h, or k_max), -1 padded. No decision
+ * log. Workspace: knn_adaptive_ds_multi_workspace_size.
+ * (Batching of requests with different k is a serving need; the paper
+ * treats one query at a time.)
+ */
+size_t knn_adaptive_ds_multi_workspace_size(const knn_dataset* ds, int32_t nq, int32_t k_max, const knn_opts* opts);
+knn_status knn_adaptive_ds_multi(const knn_dataset* ds, int32_t storage, const float* Q, int32_t nq,
+                                 const int32_t* k_per_query, int32_t k_max, const uint64_t* query_ids,
+                                 double delta, uint64_t seed, const knn_opts* opts,
+                                 int64_t* out_idx, int32_t* out_count, int64_t* out_evals, int32_t* out_rounds,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+
+/*
  * knn_rerank -- exact distances of candidate points, then top-k.
  *
  * For each query q, computes d = sum_j (X[c,j] - Q[q,j])^2 in FP64 for each

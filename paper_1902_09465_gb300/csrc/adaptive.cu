@@ -92,6 +92,10 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.nq = nq;
   a.k = k;
   a.h = o.h;
+  a.kq = nullptr;
+  a.qids = nullptr;
+  a.h_per_k = 0;
+  a.out_stride = k + o.h;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;
@@ -234,6 +238,10 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.nq = nq;
   a.k = k;
   a.h = o.h;
+  a.kq = nullptr;
+  a.qids = nullptr;
+  a.h_per_k = 0;
+  a.out_stride = k + o.h;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;

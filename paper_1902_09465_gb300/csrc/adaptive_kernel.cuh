@@ -44,7 +44,11 @@ struct AdaptiveArgs {
   int64_t n;
   int32_t m;
   int32_t nq;
-  int32_t k, h;
+  int32_t k, h;         // k (the largest k when kq is given) and h; see h_per_k
+  const int32_t* kq;    // per-query k (device, may be null: every query uses k)
+  const uint64_t* qids; // per-query id of the Philox counter (device, may be null: qid_base + q)
+  int32_t h_per_k;      // 1: each query uses h = its k; 0: every query uses h
+  int32_t out_stride;   // row length of out_idx
   int32_t bound;
   float a_c0, a_c1, c_alpha;  // host-precomputed constants of alpha(u)
   int32_t B0, B, grow;
@@ -163,7 +167,7 @@ __device__ float kth_of_union(const float* A, int na, const float* Bv, int nb, i
 
 // Sampled gather: slots [0, nact) of the active list, samples T .. Tn-1.
 template <int NT, class E>
-__device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, int q, int r, int nact, int64_t T, int64_t Tn,
+__device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
                                                const float* qs, const int32_t* idc, float* Sc, float* Cc,
                                                uint32_t* hist) {
   const int m = a.m;
@@ -175,7 +179,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, int q, int
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> lg, gl = lane & (G - 1);
   const int ppw = 32 >> lg;
-  const uint64_t qfield = (a.qid_base + (uint64_t)q) & a.mask_q;
+  const uint64_t qfield = qid & a.mask_q;
   for (int base = warp * ppw; base < nact; base += (NT / 32) * ppw) {
     const int sidx = base + grp;
     const bool valid = sidx < nact;
@@ -286,7 +290,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
 
   const int tid = threadIdx.x;
   const int64_t n = a.n;
-  const int k = a.k, kh = a.k + a.h;
   const size_t slot = blockIdx.x;
   // ping-pong halves: buffer b of this CTA starts at base + b * n
   int32_t* const ids0 = a.ws_ids + slot * 2 * (size_t)n;
@@ -302,7 +305,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     __syncthreads();
     const int q = sh.q;
     if (q >= a.nq) break;
-    int64_t* oidx = a.out_idx + (size_t)q * kh;
+    // this query's k, h and counter id (a mixed batch gives each query its own)
+    const int k = a.kq ? max(1, min(a.kq[q], a.k)) : a.k;
+    const int kh = k + (a.h_per_k ? k : a.h);
+    const uint64_t qid = a.qids ? a.qids[q] : a.qid_base + (uint64_t)q;
+    const int stride = a.out_stride;
+    int64_t* oidx = a.out_idx + (size_t)q * stride;
     int32_t* lcode = a.log_code ? a.log_code + (size_t)q * (size_t)n : nullptr;
     float* lS = a.log_S ? a.log_S + (size_t)q * (size_t)n : nullptr;
 
@@ -336,7 +344,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     }
     const float span2 = spanw * spanw;
     if (bad || !isfinite(span2)) {
-      for (int t = tid; t < kh; t += NT) oidx[t] = -1;
+      for (int t = tid; t < stride; t += NT) oidx[t] = -1;
       if (tid == 0) {
         a.out_count[q] = 0;
         a.out_evals[q] = 0;
@@ -346,7 +354,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       continue;
     }
     if (n <= kh) {  // every point is a candidate
-      for (int t = tid; t < kh; t += NT) oidx[t] = t < n ? t : -1;
+      for (int t = tid; t < stride; t += NT) oidx[t] = t < n ? t : -1;
       if (lcode)
         for (int64_t i = tid; i < n; i += NT) {
           lcode[i] = 0;
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
       else
-        gather_sampled<NT, E>(a, q, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
+        gather_sampled<NT, E>(a, qid, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
       __syncthreads();
       evals += (int64_t)nact * (exact ? (int64_t)m : Br);
       const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
@@ -549,7 +557,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     }
     __syncthreads();
     const int count = nacc_o + nact_o;
-    for (int t = tid; t < kh; t += NT) oidx[t] = t < count ? (int64_t)oid[t] : -1;
+    for (int t = tid; t < stride; t += NT) oidx[t] = t < count ? (int64_t)oid[t] : -1;
     if (lcode)
       for (int i = tid; i < nact; i += NT) {
         lcode[idf[i]] = 4 * r + 0;

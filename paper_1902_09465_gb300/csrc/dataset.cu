@@ -147,11 +147,20 @@ extern "C" knn_status knn_dataset_error(const knn_dataset* ds, int32_t storage, 
   return KNN_OK;
 }
 
+// Per-query k and counter ids of a mixed batch (null: one k, ids qid_base + q).
+struct MixedBatch {
+  const int32_t* kq = nullptr;
+  const uint64_t* qids = nullptr;
+  int32_t h_per_k = 0;
+  int32_t out_stride = 0;
+};
+
 template <class E>
 static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k, double delta,
                                      uint64_t seed, const knn_opts& o, int64_t* out_idx, int32_t* out_count,
                                      int64_t* out_evals, int32_t* out_rounds, int32_t* log_code, float* log_S,
-                                     void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+                                     void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                                     const MixedBatch* mix = nullptr) {
   const int64_t n = ds->n;
   const int32_t m = ds->m;
   AdaptivePlan p;
@@ -185,6 +194,10 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.nq = nq;
   a.k = k;
   a.h = o.h;
+  a.kq = mix ? mix->kq : nullptr;
+  a.qids = mix ? mix->qids : nullptr;
+  a.h_per_k = mix ? mix->h_per_k : 0;
+  a.out_stride = mix ? mix->out_stride : k + o.h;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;
@@ -249,4 +262,45 @@ extern "C" knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, co
                                        log_code, log_S, workspace, workspace_bytes, stream);
   return adaptive_ds_launch<ElemF32>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
                                      log_code, log_S, workspace, workspace_bytes, stream);
+}
+
+extern "C" size_t knn_adaptive_ds_multi_workspace_size(const knn_dataset* ds, int32_t nq, int32_t k_max,
+                                                       const knn_opts* opts) {
+  if (!ds) return 0;
+  return knn_adaptive_workspace_size(ds->n, ds->m, nq, k_max, opts);
+}
+
+extern "C" knn_status knn_adaptive_ds_multi(const knn_dataset* ds, int32_t storage, const float* Q, int32_t nq,
+                                            const int32_t* k_per_query, int32_t k_max, const uint64_t* query_ids,
+                                            double delta, uint64_t seed, const knn_opts* opts, int64_t* out_idx,
+                                            int32_t* out_count, int64_t* out_evals, int32_t* out_rounds,
+                                            void* workspace, size_t workspace_bytes, void* stream_) {
+  clear_error();
+  if (!ds) return set_error("knn_adaptive_ds_multi: null dataset"), KNN_EINVAL;
+  knn_opts raw;
+  knn_opts_default(&raw);
+  if (opts) raw = *opts;
+  const knn_opts o = resolve(opts, k_max);  // h resolved for the largest k: the bound on k + h
+  knn_status s = validate(ds->n, ds->m, nq, k_max, delta, o);
+  if (s != KNN_OK) return s;
+  if (storage < 0 || storage > 2) return set_error("unknown storage"), KNN_EINVAL;
+  if ((storage == KNN_STORE_BF16 && !ds->xb) || (storage == KNN_STORE_FP8 && !ds->x8))
+    return set_error("knn_adaptive_ds_multi: the dataset was created without that copy"), KNN_EINVAL;
+  if (nq == 0) return KNN_OK;
+  if (!Q || !k_per_query || !query_ids || !out_idx || !out_count || !out_evals)
+    return set_error("knn_adaptive_ds_multi: Q, k_per_query, query_ids and the outputs are required"), KNN_EINVAL;
+  MixedBatch mix;
+  mix.kq = k_per_query;
+  mix.qids = query_ids;
+  mix.h_per_k = raw.h < 0 ? 1 : 0;
+  mix.out_stride = k_max + o.h;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  if (storage == KNN_STORE_BF16)
+    return adaptive_ds_launch<ElemBF16>(ds, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
+                                        nullptr, nullptr, workspace, workspace_bytes, stream, &mix);
+  if (storage == KNN_STORE_FP8)
+    return adaptive_ds_launch<ElemFP8>(ds, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
+                                       nullptr, nullptr, workspace, workspace_bytes, stream, &mix);
+  return adaptive_ds_launch<ElemF32>(ds, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
+                                     nullptr, nullptr, workspace, workspace_bytes, stream, &mix);
 }

@@ -55,6 +55,9 @@ _SIGS = {
     "knn_exact_ds_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32]),
     "knn_exact_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "knn_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
+    "knn_adaptive_ds_multi_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32, C.POINTER(Opts)]),
+    "knn_adaptive_ds_multi": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_double, C.c_uint64,
+                                        C.POINTER(Opts), _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "knn_last_error": (C.c_char_p, []),
     "knn_version": (C.c_char_p, []),
 }
@@ -202,6 +205,34 @@ class Dataset:
                                    _dev(out["rounds"], "rounds", torch.int32),
                                    _dev(out["code"], "code", torch.int32) if trace else None,
                                    _dev(out["S"], "S") if trace else None, ws_ptr, ws_bytes, _stream(stream))
+        _check(rc)
+        return out
+
+    def multi_workspace_size(self, nq: int, k_max: int, **opt_kw) -> int:
+        o = make_opts(k_max, **opt_kw)
+        return int(lib().knn_adaptive_ds_multi_workspace_size(self._h, int(nq), int(k_max), C.byref(o)))
+
+    def adaptive_multi(self, Q: torch.Tensor, ks: torch.Tensor, k_max: int, qids: torch.Tensor, delta: float = 0.01,
+                       seed: int = 0, *, storage: str = "f32", workspace: torch.Tensor | None = None, stream=None,
+                       out=None, **opt_kw):
+        """knn_adaptive_ds_multi: a mixed batch, query q with its own k
+        (ks[q], int32 on the device) and Philox query id (qids[q], int64 on
+        the device). Rows of idx are k_max + h_max long."""
+        nq = Q.shape[0]
+        o = make_opts(k_max, **opt_kw)
+        h_max = k_max if o.h < 0 else o.h
+        if out is None:
+            out = _alloc_out(nq, self.n, k_max + h_max, Q.device, False)
+        ws_ptr, ws_bytes = None, 0
+        if workspace is not None:
+            ws_ptr, ws_bytes = _dev(workspace, "workspace", torch.uint8), workspace.numel()
+        rc = lib().knn_adaptive_ds_multi(self._h, STORAGE[storage], _dev(Q, "Q"), nq, _dev(ks, "ks", torch.int32),
+                                         int(k_max), _dev(qids, "qids", torch.int64), float(delta), int(seed),
+                                         C.byref(o), _dev(out["idx"], "idx", torch.int64),
+                                         _dev(out["count"], "count", torch.int32),
+                                         _dev(out["evals"], "evals", torch.int64),
+                                         _dev(out["rounds"], "rounds", torch.int32), ws_ptr, ws_bytes,
+                                         _stream(stream))
         _check(rc)
         return out
 

@@ -168,3 +168,35 @@ def coherent_axis(n: int, m: int, axis: int = 0, seed: int = 0):
     q = np.zeros((1, m), dtype=np.float32)
     q[0, axis] = np.float32(g.random() - 0.5)
     return X, q
+
+
+def mixture_planted(n: int, m: int, npool: int, centres: int = 64, sigma_frac: float = 0.1, kplant: int = 10,
+                    gap_lo: float = 1.2, gap_hi: float = 4.0, seed: int = 0, dfar_sample: int = 64):
+    """Gaussian mixture with planted neighbours (a resident serving dataset):
+    `centres` centres ~ N(0, I); a point is a centre plus N(0, s^2) per
+    coordinate with s = sigma_frac times the centres' per-coordinate spread
+    (1); a pool of `npool` queries is drawn from the mixture and each gets
+    `kplant` planted rows at distance D_far / g, g ~ U[gap_lo, gap_hi] and
+    D_far the query's median distance to `dfar_sample` rows.
+    Returns (X [n,m] f32, pool [npool,m] f32)."""
+    g = _rng(seed)
+    C = g.standard_normal((centres, m))
+    X = np.empty((n, m), dtype=np.float32)
+    step = 1 << 15
+    for s in range(0, n, step):
+        e = min(n, s + step)
+        c = g.integers(0, centres, size=e - s)
+        X[s:e] = (C[c] + sigma_frac * g.standard_normal((e - s, m))).astype(np.float32)
+    c = g.integers(0, centres, size=npool)
+    P = (C[c] + sigma_frac * g.standard_normal((npool, m))).astype(np.float32)
+    if npool * kplant > n:
+        raise ValueError("not enough rows to plant")
+    rows = g.permutation(n)[: npool * kplant].reshape(npool, kplant)
+    for qi in range(npool):
+        probe = X[g.integers(0, n, size=dfar_sample)].astype(np.float64)
+        dfar = float(np.median(np.sqrt(((probe - P[qi].astype(np.float64)) ** 2).sum(axis=1))))
+        r = dfar / g.uniform(gap_lo, gap_hi)
+        u = g.standard_normal((kplant, m))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        X[rows[qi]] = (P[qi].astype(np.float64)[None, :] + r * u).astype(np.float32)
+    return X, P
