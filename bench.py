@@ -456,7 +456,7 @@ def run_serve(args):
         tunes.append({"n": n, "d": m, **b})
     # warm-up: one small request per dataset
     srv = serve.Server(dss, cfgs, slots=args.serve_slots, mem_budget=args.serve_mem << 30)
-    srv.run([(0.0, r) for r in serve.poisson_requests(200.0, 0.05, pools, max_queries=8, seed=7)[:8]])
+    srv.run(serve.poisson_requests(200.0, 0.05, pools, max_queries=8, seed=7)[:8])
 
     phases = {}
     rates = [SERVE["rate"]]
