@@ -166,69 +166,102 @@ __device__ float kth_of_union(const float* A, int na, const float* Bv, int nb, i
 }
 
 // Sampled gather: slots [0, nact) of the active list, samples T .. Tn-1.
+// G lanes share a point (G = blocks of 8 draws this round, rounded up to a
+// power of two, at most 32); each lane walks its blocks of its points as one
+// flat sequence of items and computes the next item's Philox block while the
+// current item's 8 loads are in flight (software pipelining over items).
 template <int NT, class E>
 __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
                                                const float* qs, const int32_t* idc, float* Sc, float* Cc,
                                                uint32_t* hist) {
+  using Tp = typename E::T;
   const int m = a.m;
   const uint64_t blo = (uint64_t)T >> 3, bhi = (uint64_t)(Tn - 1) >> 3;
   const int nblk = (int)(bhi - blo + 1);
   int G = 1;
   while (G < nblk && G < 32) G <<= 1;
   const int lg = __ffs(G) - 1;
+  const int nbl = (nblk + G - 1) / G;  // blocks per lane per point
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> lg, gl = lane & (G - 1);
   const int ppw = 32 >> lg;
+  const int pstride = (NT / 32) * ppw;
   const uint64_t qfield = qid & a.mask_q;
-  for (int base = warp * ppw; base < nact; base += (NT / 32) * ppw) {
-    const int sidx = base + grp;
-    const bool valid = sidx < nact;
-    float part = 0.0f;
-    if (valid) {
-      const int id = (r == 0) ? sidx : idc[sidx];
-      const typename E::T* xr = static_cast<const typename E::T*>(a.G) + (size_t)id * (size_t)m;
-      const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
-      const uint64_t pfield = (uint64_t)id & a.mask_p;
-      for (uint64_t b = blo + gl; b <= bhi; b += G) {
-        const Philox4x64 ph = philox4x64_10(b, pfield, qfield, 0, a.seed, 0);
-        const int64_t s0 = (int64_t)(b << 3);
-        float xv[8];
-        int jj[8];
-        bool ok[8];
+  const Tp* G0 = static_cast<const Tp*>(a.G);
+  // items of this lane: t = pair_iter * nbl + j, point slot warp*ppw + grp + pair_iter*pstride, block blo + gl + j*G
+  const int first = warp * ppw;
+  const int npairs = first < nact ? (nact - first + pstride - 1) / pstride : 0;  // warp-uniform
+  const int nitems = npairs * nbl;
+  if (nitems == 0) return;
+  // item state: slot, point id, block, and its Philox output
+  auto item = [&](int t, int& sidx, int& id, uint64_t& b, bool& has) {
+    const int pi = t / nbl, j = t - pi * nbl;
+    sidx = first + grp + pi * pstride;
+    b = blo + (uint64_t)(gl + j * G);
+    has = sidx < nact && b <= bhi;
+    id = has ? ((r == 0) ? sidx : idc[sidx]) : 0;
+  };
+  int sidx, id;
+  uint64_t b;
+  bool has;
+  item(0, sidx, id, b, has);
+  Philox4x64 ph = has ? philox4x64_10(b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0) : Philox4x64{};
+  float part = 0.0f;
+  for (int t = 0; t < nitems; ++t) {
+    // issue the current item's loads
+    float xv[8];
+    int jj[8];
+    bool ok[8];
+    const Tp* xr = G0 + (size_t)id * (size_t)m;
+    const int64_t s0 = (int64_t)(b << 3);
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          const int64_t s = s0 + w;
-          ok[w] = (s >= T) && (s < Tn);
-          jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
-          xv[w] = ok[w] ? E::load(xr + jj[w]) : 0.0f;
-        }
+    for (int w = 0; w < 8; ++w) {
+      const int64_t s = s0 + w;
+      ok[w] = has && (s >= T) && (s < Tn);
+      jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+      xv[w] = ok[w] ? E::load(xr + jj[w]) : 0.0f;
+    }
+    const float sc = (E::kScaled && has) ? __ldg(a.gscale + id) : 1.0f;
+    const int cur_sidx = sidx;
+    const bool cur_has = has;
+    // the next item's Philox while the loads are in flight
+    if (t + 1 < nitems) {
+      item(t + 1, sidx, id, b, has);
+      if (has) ph = philox4x64_10(b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0);
+    }
+    // consume
+    if (cur_has) {
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          if (ok[w]) {
-            const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
-            part = fmaf(d, d, part);
-          }
+      for (int w = 0; w < 8; ++w) {
+        if (ok[w]) {
+          const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
+          part = fmaf(d, d, part);
         }
       }
     }
+    if ((t + 1) % nbl == 0) {  // last block of this point: combine the G lanes and store
 #pragma unroll
-    for (int o = 16; o; o >>= 1)
-      if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (valid && gl == 0) {
-      float S;
-      if (r == 0) {
-        S = part;
-      } else {
-        // Kahan-compensated running sum
-        const float S0 = Sc[sidx], c0 = Cc[sidx];
-        const float y = part - c0;
-        const float t = S0 + y;
-        Cc[sidx] = (t - S0) - y;
-        S = t;
+      for (int o = 16; o; o >>= 1)
+        if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const int ps = first + grp + (t / nbl) * pstride;
+      if (ps < nact && gl == 0) {
+        float S;
+        if (r == 0) {
+          S = part;
+        } else {
+          // Kahan-compensated running sum
+          const float S0 = Sc[ps], c0 = Cc[ps];
+          const float y = part - c0;
+          const float tt = S0 + y;
+          Cc[ps] = (tt - S0) - y;
+          S = tt;
+        }
+        Sc[ps] = S;
+        atomicAdd(&hist[f2key(S) >> 20], 1u);
       }
-      Sc[sidx] = S;
-      atomicAdd(&hist[f2key(S) >> 20], 1u);
+      part = 0.0f;
     }
+    (void)cur_sidx;
   }
 }
 
