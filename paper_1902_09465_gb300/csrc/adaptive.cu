@@ -29,7 +29,9 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
   AdaptivePlan p;
   if (plan_adaptive<ElemF32>(n, m, nq, k, &o, &p) != KNN_OK) return 0;
   Carve cv;
-  return carve_adaptive(cv, n, p, nullptr) + 256;
+  carve_adaptive(cv, n, p, nullptr);
+  if (round0_applies(m, o)) cv.take<float>((size_t)round0_chunk(n, nq) * (size_t)n);  // dataset path only
+  return cv.off + 256;
 }
 
 extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
@@ -96,6 +98,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.qids = nullptr;
   a.h_per_k = 0;
   a.out_stride = k + o.h;
+  a.R0 = nullptr;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;
@@ -242,6 +245,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.qids = nullptr;
   a.h_per_k = 0;
   a.out_stride = k + o.h;
+  a.R0 = nullptr;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;

@@ -70,6 +70,7 @@ struct AdaptiveArgs {
   int32_t* log_code;
   float* log_S;
   int32_t vec;  // rows of X start on 16-byte boundaries: exact rows use 16-byte loads
+  const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
 };
 
 // Element access of the gathered copy. A stored BF16 value is the top half of
@@ -410,12 +411,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       const bool exact = T + Br >= m;
       const int64_t Tn = exact ? m : T + Br;
       const int32_t* idc = ids0 + (size_t)cur * n;
-      float* Sc = S0 + (size_t)cur * n;
+      const bool pre = (r == 0) && a.R0 && !exact;  // round-0 sums computed point-major beforehand
+      float* Sc = pre ? const_cast<float*>(a.R0) + (size_t)q * (size_t)n : S0 + (size_t)cur * n;
       float* Cc = C0 + (size_t)cur * n;
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
       if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
+      else if (pre)
+        for (int i = tid; i < nact; i += NT) atomicAdd(&hist[f2key(Sc[i]) >> 20], 1u);
       else
         gather_sampled<NT, E>(a, qid, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
       __syncthreads();
@@ -605,6 +609,72 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   }
 }
 
+// Round 0 for every query of a batch, point-major: a CTA stages a tile of
+// rows of the gathered copy in shared memory (dequantised to FP32) and
+// computes the round-0 sums of all queries for those rows, so the copy
+// streams from DRAM once per batch instead of being sampled at random per
+// query. Draws, lane grouping (G lanes per point, one block of 8 draws each)
+// and the shuffle reduction are those of gather_sampled, so the sums are the
+// same bit for bit. Needs B0 <= 256 (at most 32 blocks).
+constexpr int kR0Threads = 256;
+constexpr int kR0MaxRows = 32;
+constexpr size_t kR0SmemBudget = 110 * 1024;
+
+static inline int round0_rows(int m) {
+  const int r = (int)(kR0SmemBudget / ((size_t)m * 4));
+  return r < 1 ? 1 : (r > kR0MaxRows ? kR0MaxRows : r);
+}
+
+template <class E>
+__global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int rows_per_cta, float* R0) {
+  extern __shared__ __align__(16) float rows[];
+  using Tp = typename E::T;
+  const int m = a.m;
+  const int64_t n = a.n;
+  const int64_t p0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int np = (int)((n - p0) < rows_per_cta ? (n - p0) : rows_per_cta);
+  const Tp* G0 = static_cast<const Tp*>(a.G);
+  for (int e = threadIdx.x; e < np * m; e += kR0Threads) {
+    const int pi = e / m, j = e - pi * m;
+    const float x = E::load(G0 + (size_t)(p0 + pi) * m + j);
+    rows[e] = E::kScaled ? __fmul_rn(x, __ldg(a.gscale + p0 + pi)) : x;
+  }
+  __syncthreads();
+  const int nblk = (a.B0 + 7) >> 3;
+  int G = 1;
+  while (G < nblk && G < 32) G <<= 1;
+  const int lg = __ffs(G) - 1;
+  const int ppw = 32 >> lg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane >> lg, gl = lane & (G - 1);
+  for (int q = warp; q < a.nq; q += kR0Threads / 32) {
+    const uint64_t qid = a.qids ? a.qids[q] : a.qid_base + (uint64_t)q;
+    const uint64_t qfield = qid & a.mask_q;
+    const float* qr = a.Q + (size_t)q * m;
+    for (int base = 0; base < np; base += ppw) {
+      const int pi = base + grp;
+      float part = 0.0f;
+      if (pi < np && gl < nblk) {
+        const uint64_t id = (uint64_t)(p0 + pi);
+        const Philox4x64 ph = philox4x64_10((uint64_t)gl, id & a.mask_p, qfield, 0, a.seed, 0);
+        const float* xr = rows + (size_t)pi * m;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          if (gl * 8 + w < a.B0) {
+            const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+            const float d = xr[j] - __ldg(qr + j);
+            part = fmaf(d, d, part);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1)
+        if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (pi < np && gl == 0) R0[(size_t)q * (size_t)n + p0 + pi] = part;
+    }
+  }
+}
+
 // Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and
 // xr[2] = 1 if any element is NaN or infinite.
 static __global__ void minmax_kernel(const float* __restrict__ X, size_t count, uint32_t* xr) {
@@ -723,6 +793,17 @@ static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, Adapti
   c.acc_L = cv.take<float>(acc);
   if (out) *out = c;
   return cv.off;
+}
+
+// Round-0 sums of a chunk of queries (the point-major round-0 pass), at
+// most kR0BufferBytes: the query chunk is sized to fit.
+constexpr size_t kR0BufferBytes = size_t(1) << 30;
+
+static inline bool round0_applies(int32_t m, const knn_opts& o) { return o.B0 < m && o.B0 <= 256; }
+
+static inline int round0_chunk(int64_t n, int32_t nq) {
+  const int64_t c = (int64_t)(kR0BufferBytes / (4 * (size_t)n));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(nq, c));
 }
 
 static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double delta, const knn_opts& o) {

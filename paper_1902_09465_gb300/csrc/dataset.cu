@@ -163,11 +163,15 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
                                      const MixedBatch* mix = nullptr) {
   const int64_t n = ds->n;
   const int32_t m = ds->m;
+  const bool r0 = round0_applies(m, o);
+  const int chunk = r0 ? round0_chunk(n, nq) : nq;
   AdaptivePlan p;
-  knn_status s = plan_adaptive<E>(n, m, nq, k, &o, &p);
+  knn_status s = plan_adaptive<E>(n, m, chunk, k, &o, &p);
   if (s != KNN_OK) return s;
   Carve measure;
-  const size_t need = carve_adaptive(measure, n, p, nullptr) + 256;
+  carve_adaptive(measure, n, p, nullptr);
+  if (r0) measure.take<float>((size_t)chunk * (size_t)n);
+  const size_t need = measure.off + 256;
   Workspace ws;
   s = ws.acquire(workspace, workspace_bytes, need, stream);
   if (s != KNN_OK) return s;
@@ -175,11 +179,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   cv.base = reinterpret_cast<uint8_t*>(((uintptr_t)ws.ptr + 255) & ~uintptr_t(255));
   AdaptiveCarve c;
   carve_adaptive(cv, n, p, &c);
-  s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
-  if (s != KNN_OK) {
-    ws.release();
-    return s;
-  }
+  float* r0buf = r0 ? cv.take<float>((size_t)chunk * (size_t)n) : nullptr;
   AdaptiveArgs a;
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
@@ -233,7 +233,40 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)ds->X & 15) == 0);
-  s = launch_rounds<E>(p, a, stream);
+  a.R0 = r0buf;
+  const int rows = round0_rows(m);
+  if (r0) {
+    s = cuda_check(cudaFuncSetAttribute(round0_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((size_t)rows * m * 4)),
+                   "cudaFuncSetAttribute(round0)");
+    if (s != KNN_OK) {
+      ws.release();
+      return s;
+    }
+  }
+  // queries in chunks whose round-0 sums fit the buffer: round 0 point-major,
+  // then the remaining rounds of the chunk's queries
+  for (int32_t q0 = 0; q0 < nq && s == KNN_OK; q0 += chunk) {
+    AdaptiveArgs ac = a;
+    ac.nq = std::min(chunk, nq - q0);
+    ac.Q = Q + (size_t)q0 * m;
+    ac.out_idx = out_idx + (size_t)q0 * a.out_stride;
+    ac.out_count = out_count + q0;
+    ac.out_evals = out_evals + q0;
+    ac.out_rounds = out_rounds ? out_rounds + q0 : nullptr;
+    ac.log_code = log_code ? log_code + (size_t)q0 * n : nullptr;
+    ac.log_S = a.log_S ? a.log_S + (size_t)q0 * n : nullptr;
+    ac.kq = a.kq ? a.kq + q0 : nullptr;
+    ac.qids = a.qids ? a.qids + q0 : nullptr;
+    ac.qid_base = a.qid_base + (uint64_t)q0;
+    s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
+    if (s == KNN_OK && r0) {
+      const unsigned blocks = (unsigned)((n + rows - 1) / rows);
+      round0_kernel<E><<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf);
+      s = cuda_check(cudaGetLastError(), "round0_kernel launch");
+    }
+    if (s == KNN_OK) s = launch_rounds<E>(p, ac, stream);
+  }
   ws.release();
   return s;
 }
