@@ -126,6 +126,8 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
                     break
             if chosen is None:
                 continue
+            res = ds.adaptive(H, k, delta, 0, storage=storage, c_alpha=chosen, **opts)  # untimed warm-up
+            knn.rerank(ds.X, H, res["idx"], k)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
