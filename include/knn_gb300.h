@@ -181,6 +181,22 @@ knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, const float* 
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * knn_dataset_share -- shared coordinates. With both Philox counter masks of
+ * the options zero (mask_p = mask_q = 0) every (query, point) pair of a seed
+ * draws the same coordinate sequence j_0, j_1, ..., so a point's first T draws
+ * are the first T columns of a copy whose column t is column j_t of the data.
+ * This builds that copy for `seed` and each storage in `copies` (bit mask of
+ * 1 << KNN_STORE_*; BF16/FP8 need those copies in the dataset), rows padded to
+ * a multiple of 8, and waits for it. knn_adaptive_ds(_multi) then reads
+ * contiguous row prefixes instead of drawing and gathering, with the same
+ * results bit for bit. (Each point's samples are still uniform draws with
+ * replacement, as Lemma "probound" needs; points share them, which the
+ * per-point union bound allows.) A later call with another seed replaces the
+ * copies.
+ */
+knn_status knn_dataset_share(knn_dataset* ds, uint64_t seed, int32_t copies, void* stream);
+
+/*
  * knn_adaptive_ds_multi -- one launch over a mixed batch: query q uses its
  * own k = k_per_query[q] (1 <= k <= k_max) and its own Philox query id
  * query_ids[q] (both device arrays), so a query's draws, decisions and

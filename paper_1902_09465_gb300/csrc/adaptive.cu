@@ -99,6 +99,8 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.h_per_k = 0;
   a.out_stride = k + o.h;
   a.R0 = nullptr;
+  a.jperm = nullptr;
+  a.mp = 0;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;
@@ -246,6 +248,8 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.h_per_k = 0;
   a.out_stride = k + o.h;
   a.R0 = nullptr;
+  a.jperm = nullptr;
+  a.mp = 0;
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;

@@ -71,6 +71,8 @@ struct AdaptiveArgs {
   float* log_S;
   int32_t vec;  // rows of X start on 16-byte boundaries: exact rows use 16-byte loads
   const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
+  const int32_t* jperm; // shared-coordinate copies: column of draw t (t < m), for Perm element types
+  int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
 };
 
 // Element access of the gathered copy. A stored BF16 value is the top half of
@@ -82,6 +84,7 @@ struct ElemF32 {
   using T = float;
   static constexpr int kStorage = KNN_STORE_F32;
   static constexpr bool kScaled = false;
+  static constexpr bool kPerm = false;
   __device__ static __forceinline__ float load(const T* p) { return __ldg(p); }
   __device__ static __forceinline__ float conv(T v) { return v; }
 };
@@ -89,6 +92,7 @@ struct ElemBF16 {
   using T = uint16_t;
   static constexpr int kStorage = KNN_STORE_BF16;
   static constexpr bool kScaled = false;
+  static constexpr bool kPerm = false;
   __device__ static __forceinline__ float conv(T v) { return __uint_as_float((uint32_t)v << 16); }
   __device__ static __forceinline__ float load(const T* p) { return conv(__ldg(p)); }
 };
@@ -96,6 +100,7 @@ struct ElemFP8 {
   using T = uint8_t;
   static constexpr int kStorage = KNN_STORE_FP8;
   static constexpr bool kScaled = true;
+  static constexpr bool kPerm = false;
   __device__ static __forceinline__ float conv(T v) {
     __nv_fp8_e4m3 f;
     f.__x = v;
@@ -115,6 +120,37 @@ struct AdaptiveShared {
   int bad;
   float tauU, tauL;
 };
+
+// Shared coordinates (both counter masks zero): every pair draws the same
+// coordinate sequence j_0, j_1, ... for a seed, so a point's first T draws are
+// the first T columns of a copy whose column t holds column j_t of the data.
+// Rounds then read contiguous row prefixes instead of drawing and gathering.
+template <class Base>
+struct Perm : Base {
+  static constexpr bool kPerm = true;
+};
+
+// 8 consecutive elements of a shared-coordinate row (16-byte aligned blocks
+// for FP32 and BF16, 8-byte for FP8), converted to FP32.
+template <class E>
+__device__ __forceinline__ void load8(const typename E::T* p, float* x) {
+  if constexpr (sizeof(typename E::T) == 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+  } else if constexpr (sizeof(typename E::T) == 2) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = E::conv((typename E::T)(w[i >> 1] >> (16 * (i & 1))));
+  } else {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    const uint32_t w[2] = {v.x, v.y};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = E::conv((typename E::T)(w[i >> 2] >> (8 * (i & 3))));
+  }
+}
 
 // alpha(u) in normalised units. c0/c1 carry the delta- and n-dependent
 // constants computed on the host in double precision.
@@ -182,6 +218,52 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
   int G = 1;
   while (G < nblk && G < 32) G <<= 1;
   const int lg = __ffs(G) - 1;
+  if constexpr (E::kPerm) {
+    // shared coordinates: row prefixes of the permuted copy; qs here holds the
+    // query permuted the same way. Same lanes, order and reduction as below.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane >> lg, gl = lane & (G - 1);
+    const int ppw = 32 >> lg;
+    for (int base = warp * ppw; base < nact; base += (NT / 32) * ppw) {
+      const int sidx = base + grp;
+      float part = 0.0f;
+      if (sidx < nact) {
+        const int id = (r == 0) ? sidx : idc[sidx];
+        const Tp* xr = static_cast<const Tp*>(a.G) + (size_t)id * (size_t)a.mp;
+        const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
+        for (uint64_t b = blo + gl; b <= bhi; b += G) {
+          float x[8];
+          load8<E>(xr + 8 * b, x);
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            const int64_t s = (int64_t)(8 * b) + w;
+            if (s >= T && s < Tn) {
+              const float d = (E::kScaled ? __fmul_rn(x[w], sc) : x[w]) - qs[s];
+              part = fmaf(d, d, part);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1)
+        if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (sidx < nact && gl == 0) {
+        float S;
+        if (r == 0) {
+          S = part;
+        } else {
+          const float S0 = Sc[sidx], c0 = Cc[sidx];
+          const float y = part - c0;
+          const float tt = S0 + y;
+          Cc[sidx] = (tt - S0) - y;
+          S = tt;
+        }
+        Sc[sidx] = S;
+        atomicAdd(&hist[f2key(S) >> 20], 1u);
+      }
+    }
+    return;
+  }
   const int nbl = (nblk + G - 1) / G;  // blocks per lane per point
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int grp = lane >> lg, gl = lane & (G - 1);
@@ -319,6 +401,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   float* actU = reinterpret_cast<float*>(buf + kSelCap);
   float* actL = actU + (kMaxKH + 4);
   int32_t* oid = reinterpret_cast<int32_t*>(actL + (kMaxKH + 4));
+  float* qsp = reinterpret_cast<float*>(oid + kMaxKH);  // permuted query (shared coordinates only)
   float* tmpS = actU;                              // reused in the output phase
   int32_t* tmpI = reinterpret_cast<int32_t*>(actL);
 
@@ -361,6 +444,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     }
     for (int j = m + tid; j < mpad; j += NT) qs[j] = 0.0f;
     bad = __syncthreads_or(bad);
+    if constexpr (E::kPerm) {
+      for (int t = tid; t < a.mp; t += NT) qsp[t] = t < m ? qs[a.jperm[t]] : 0.0f;
+      __syncthreads();
+    }
     qmin = block_min<NT>(qmin, sh.bs);
     qmax = block_max<NT>(qmax, sh.bs);
     const float xmin = key2f(a.xrange[0]), xmax = key2f(a.xrange[1]);
@@ -421,7 +508,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       else if (pre)
         for (int i = tid; i < nact; i += NT) atomicAdd(&hist[f2key(Sc[i]) >> 20], 1u);
       else
-        gather_sampled<NT, E>(a, qid, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
+        gather_sampled<NT, E>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
       evals += (int64_t)nact * (exact ? (int64_t)m : Br);
       const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
@@ -707,10 +794,11 @@ static __global__ void minmax_kernel(const float* __restrict__ X, size_t count, 
 
 constexpr int kAdaptiveNT = 512;  // default threads per CTA (256 is the other choice)
 
-static size_t adaptive_smem_bytes(int m) {
+static size_t adaptive_smem_bytes(int m, bool perm = false) {
   const size_t mpad = (size_t)((m + 3) & ~3);
+  const size_t mp = (size_t)((m + 7) & ~7);
   return mpad * 4 + (size_t)kHistBins * 4 + (size_t)kSelCap * 4 + 2 * (size_t)(kMaxKH + 4) * 4 +
-         (size_t)kMaxKH * 4;
+         (size_t)kMaxKH * 4 + (perm ? mp * 4 : 0);
 }
 
 struct AdaptivePlan {
@@ -734,7 +822,7 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   knn_status s = device_info(&di);
   if (s != KNN_OK) return s;
   p->threads = (o && o->threads == 256) ? 256 : kAdaptiveNT;
-  p->smem = adaptive_smem_bytes(m);
+  p->smem = adaptive_smem_bytes(m, E::kPerm);
   const void* fn = rounds_kernel_for<E>(p->threads);
   s = cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
                  "cudaFuncSetAttribute(adaptive)");

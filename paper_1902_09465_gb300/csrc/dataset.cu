@@ -62,6 +62,26 @@ static __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t 
   if (lane == 0) atomicMax(emax_bits, __float_as_uint(e));
 }
 
+// Column of draw t under shared coordinates: Philox4x64-10 with key
+// (seed, 0) and counter (t / 8, 0, 0, 0), word t mod 8 scaled to [0, m).
+static __global__ void shared_columns_kernel(uint64_t seed, int m, int32_t* jperm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const Philox4x64 ph = philox4x64_10((uint64_t)t >> 3, 0, 0, 0, seed, 0);
+  jperm[t] = (int32_t)__umulhi(philox_word(ph, t & 7), (uint32_t)m);
+}
+
+// Permuted copy: out[i, t] = src[i, jperm[t]] for t < m, zero up to mp.
+template <class T>
+static __global__ void permute_rows_kernel(const T* __restrict__ src, int64_t n, int m, int mp,
+                                           const int32_t* __restrict__ jperm, T* __restrict__ out) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const T* sr = src + (size_t)i * m;
+    T* orow = out + (size_t)i * mp;
+    for (int t = threadIdx.x; t < mp; t += blockDim.x) orow[t] = t < m ? sr[jperm[t]] : T(0);
+  }
+}
+
 }  // namespace knn
 
 using namespace knn;
@@ -134,6 +154,10 @@ extern "C" knn_status knn_dataset_destroy(knn_dataset* ds) {
   cudaFree(ds->mu);
   cudaFree(ds->xcn);
   cudaFree(ds->xcn_max);
+  cudaFree(ds->jperm);
+  cudaFree(ds->p32);
+  cudaFree(ds->pb);
+  cudaFree(ds->p8);
   cudaSetDevice(cur);
   delete ds;
   return KNN_OK;
@@ -163,7 +187,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
                                      const MixedBatch* mix = nullptr) {
   const int64_t n = ds->n;
   const int32_t m = ds->m;
-  const bool r0 = round0_applies(m, o);
+  const bool r0 = !E::kPerm && round0_applies(m, o);
   const int chunk = r0 ? round0_chunk(n, nq) : nq;
   AdaptivePlan p;
   knn_status s = plan_adaptive<E>(n, m, chunk, k, &o, &p);
@@ -184,6 +208,8 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
   if (E::kStorage == KNN_STORE_FP8) G = ds->x8;
+  if (E::kPerm) G = E::kStorage == KNN_STORE_BF16 ? (const void*)ds->pb
+                    : (E::kStorage == KNN_STORE_FP8 ? (const void*)ds->p8 : (const void*)ds->p32);
   a.X = ds->X;
   a.G = G;
   a.gscale = ds->scale8;
@@ -234,6 +260,8 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)ds->X & 15) == 0);
   a.R0 = r0buf;
+  a.jperm = ds->jperm;
+  a.mp = ds->mp;
   const int rows = round0_rows(m);
   if (r0) {
     s = cuda_check(cudaFuncSetAttribute(round0_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -271,6 +299,28 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   return s;
 }
 
+// Element type of the launch: the shared-coordinate copy when both counter
+// masks are zero and the dataset holds that copy for this seed, else the
+// stored copy with per-pair draws.
+static knn_status dispatch_ds(const knn_dataset* ds, int32_t storage, const float* Q, int32_t nq, int32_t k,
+                              double delta, uint64_t seed, const knn_opts& o, int64_t* out_idx, int32_t* out_count,
+                              int64_t* out_evals, int32_t* out_rounds, int32_t* log_code, float* log_S,
+                              void* workspace, size_t workspace_bytes, cudaStream_t stream, const MixedBatch* mix) {
+  const bool shared = o.mask_p == 0 && o.mask_q == 0 && ((ds->share_ready >> storage) & 1) && ds->share_seed == seed;
+#define KNN_DS_LAUNCH(E)                                                                                        \
+  return adaptive_ds_launch<E>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds, log_code, \
+                               log_S, workspace, workspace_bytes, stream, mix)
+  if (shared) {
+    if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(Perm<ElemBF16>);
+    if (storage == KNN_STORE_FP8) KNN_DS_LAUNCH(Perm<ElemFP8>);
+    KNN_DS_LAUNCH(Perm<ElemF32>);
+  }
+  if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(ElemBF16);
+  if (storage == KNN_STORE_FP8) KNN_DS_LAUNCH(ElemFP8);
+  KNN_DS_LAUNCH(ElemF32);
+#undef KNN_DS_LAUNCH
+}
+
 extern "C" knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, const float* Q, int32_t nq, int32_t k,
                                       double delta, uint64_t seed, const knn_opts* opts, int64_t* out_idx,
                                       int32_t* out_count, int64_t* out_evals, int32_t* out_rounds, int32_t* log_code,
@@ -287,14 +337,8 @@ extern "C" knn_status knn_adaptive_ds(const knn_dataset* ds, int32_t storage, co
   if (!Q || !out_idx || !out_count || !out_evals)
     return set_error("Q, out_idx, out_count and out_evals are required"), KNN_EINVAL;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-  if (storage == KNN_STORE_BF16)
-    return adaptive_ds_launch<ElemBF16>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
-                                        log_code, log_S, workspace, workspace_bytes, stream);
-  if (storage == KNN_STORE_FP8)
-    return adaptive_ds_launch<ElemFP8>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
-                                       log_code, log_S, workspace, workspace_bytes, stream);
-  return adaptive_ds_launch<ElemF32>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
-                                     log_code, log_S, workspace, workspace_bytes, stream);
+  return dispatch_ds(ds, storage, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds, log_code,
+                     log_S, workspace, workspace_bytes, stream, nullptr);
 }
 
 extern "C" size_t knn_adaptive_ds_multi_workspace_size(const knn_dataset* ds, int32_t nq, int32_t k_max,
@@ -328,12 +372,47 @@ extern "C" knn_status knn_adaptive_ds_multi(const knn_dataset* ds, int32_t stora
   mix.h_per_k = raw.h < 0 ? 1 : 0;
   mix.out_stride = k_max + o.h;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-  if (storage == KNN_STORE_BF16)
-    return adaptive_ds_launch<ElemBF16>(ds, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
-                                        nullptr, nullptr, workspace, workspace_bytes, stream, &mix);
-  if (storage == KNN_STORE_FP8)
-    return adaptive_ds_launch<ElemFP8>(ds, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
-                                       nullptr, nullptr, workspace, workspace_bytes, stream, &mix);
-  return adaptive_ds_launch<ElemF32>(ds, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds,
-                                     nullptr, nullptr, workspace, workspace_bytes, stream, &mix);
+  return dispatch_ds(ds, storage, Q, nq, k_max, delta, seed, o, out_idx, out_count, out_evals, out_rounds, nullptr,
+                     nullptr, workspace, workspace_bytes, stream, &mix);
+}
+
+extern "C" knn_status knn_dataset_share(knn_dataset* ds, uint64_t seed, int32_t copies, void* stream_) {
+  clear_error();
+  if (!ds) return set_error("knn_dataset_share: null dataset"), KNN_EINVAL;
+  if (copies & ~((1 << KNN_STORE_F32) | (1 << KNN_STORE_BF16) | (1 << KNN_STORE_FP8)))
+    return set_error("knn_dataset_share: copies must be a mask of F32, BF16 and FP8"), KNN_EINVAL;
+  if (((copies >> KNN_STORE_BF16) & 1) && !ds->xb)
+    return set_error("knn_dataset_share: the dataset has no BF16 copy"), KNN_EINVAL;
+  if (((copies >> KNN_STORE_FP8) & 1) && !ds->x8)
+    return set_error("knn_dataset_share: the dataset has no FP8 copy"), KNN_EINVAL;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int64_t n = ds->n;
+  const int m = ds->m;
+  ds->mp = (m + 7) & ~7;
+  const size_t cnt = (size_t)n * (size_t)ds->mp;
+  knn_status s = KNN_OK;
+  if (!ds->jperm) s = cuda_check(cudaMalloc(&ds->jperm, (size_t)m * 4), "cudaMalloc(columns)");
+  if (s == KNN_OK && ((copies >> KNN_STORE_F32) & 1) && !ds->p32)
+    s = cuda_check(cudaMalloc(&ds->p32, cnt * 4), "cudaMalloc(shared F32 copy)");
+  if (s == KNN_OK && ((copies >> KNN_STORE_BF16) & 1) && !ds->pb)
+    s = cuda_check(cudaMalloc(&ds->pb, cnt * 2), "cudaMalloc(shared BF16 copy)");
+  if (s == KNN_OK && ((copies >> KNN_STORE_FP8) & 1) && !ds->p8)
+    s = cuda_check(cudaMalloc(&ds->p8, cnt), "cudaMalloc(shared FP8 copy)");
+  if (s != KNN_OK) return s;
+  ds->share_ready = 0;
+  shared_columns_kernel<<<(m + 255) / 256, 256, 0, stream>>>(seed, m, ds->jperm);
+  DeviceInfo di;
+  s = device_info(&di);
+  if (s != KNN_OK) return s;
+  const int blocks = (int)std::min<int64_t>(n, (int64_t)di.sms * 16);
+  if ((copies >> KNN_STORE_F32) & 1) permute_rows_kernel<float><<<blocks, 256, 0, stream>>>(ds->X, n, m, ds->mp, ds->jperm, ds->p32);
+  if ((copies >> KNN_STORE_BF16) & 1) permute_rows_kernel<uint16_t><<<blocks, 256, 0, stream>>>(ds->xb, n, m, ds->mp, ds->jperm, ds->pb);
+  if ((copies >> KNN_STORE_FP8) & 1) permute_rows_kernel<uint8_t><<<blocks, 256, 0, stream>>>(ds->x8, n, m, ds->mp, ds->jperm, ds->p8);
+  s = cuda_check(cudaGetLastError(), "shared-coordinate kernels");
+  if (s == KNN_OK) s = cuda_check(cudaStreamSynchronize(stream), "shared-coordinate build");
+  if (s == KNN_OK) {
+    ds->share_seed = seed;
+    ds->share_ready = copies;
+  }
+  return s;
 }

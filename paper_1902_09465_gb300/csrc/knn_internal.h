@@ -75,4 +75,12 @@ struct knn_dataset {
   float* mu = nullptr;        // column means
   float* xcn = nullptr;       // ||x_i - mu||^2
   unsigned* xcn_max = nullptr;  // largest of them, float bits
+  // shared-coordinate copies for one seed: column t holds column jperm[t]
+  uint64_t share_seed = 0;
+  int32_t share_ready = 0;    // bit s set: the copy of storage s is built
+  int32_t mp = 0;             // row pitch (m rounded up to 8)
+  int32_t* jperm = nullptr;
+  float* p32 = nullptr;
+  uint16_t* pb = nullptr;
+  uint8_t* p8 = nullptr;
 };

@@ -58,6 +58,7 @@ _SIGS = {
     "knn_adaptive_ds_multi_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32, C.POINTER(Opts)]),
     "knn_adaptive_ds_multi": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_double, C.c_uint64,
                                         C.POINTER(Opts), _P, _P, _P, _P, _P, C.c_size_t, _P]),
+    "knn_dataset_share": (C.c_int, [_P, C.c_uint64, C.c_int32, _P]),
     "knn_last_error": (C.c_char_p, []),
     "knn_version": (C.c_char_p, []),
 }
@@ -207,6 +208,14 @@ class Dataset:
                                    _dev(out["S"], "S") if trace else None, ws_ptr, ws_bytes, _stream(stream))
         _check(rc)
         return out
+
+    def share(self, seed: int, copies=("f32",), stream=None):
+        """knn_dataset_share: shared-coordinate copies for `seed` (used by
+        adaptive calls with share_points=True, share_queries=True and that seed)."""
+        mask = 0
+        for c in copies:
+            mask |= 1 << STORAGE[c]
+        _check(lib().knn_dataset_share(self._h, int(seed), mask, _stream(stream)))
 
     def multi_workspace_size(self, nq: int, k_max: int, **opt_kw) -> int:
         o = make_opts(k_max, **opt_kw)

@@ -94,15 +94,18 @@ def tune_key(ds: knn.Dataset, k: int, storage: str) -> str:
 
 def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, storage: str = "f32",
              target: float = 0.999, margin: float = 0.0005, schedules=DEFAULT_SCHEDULES, threads=(512, 256),
-             c_grid=DEFAULT_C_GRID, reps: int = 3, cache: str | None = None, use_cache: bool = True):
+             c_grid=DEFAULT_C_GRID, reps: int = 3, cache: str | None = None, use_cache: bool = True,
+             seed: int = 0, extra=None):
     """Picks (B0, B, grow, threads, C_alpha) for a dataset: for every
     schedule and thread count, the smallest C_alpha of the grid whose recall
     on the held-out queries H (after the FP64 rerank) is at least
     target + margin, then the fastest of those. Returns a dict with the
     choice and the whole table, and stores it in the JSON cache under a key of
-    (d, n bucket, storage, k)."""
+    (d, n bucket, storage, k). `extra` adds options to every call (for
+    example the shared-coordinate masks); `seed` is the Philox seed used."""
     path = _cache_path(cache)
-    key = tune_key(ds, k, storage)
+    extra = dict(extra or {})
+    key = tune_key(ds, k, storage) + ("|" + ",".join(f"{a}={b}" for a, b in sorted(extra.items())) if extra else "")
     if use_cache and os.path.exists(path):
         try:
             with open(path) as f:
@@ -115,10 +118,10 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
     table = []
     for (B0, B, grow) in schedules:
         for th in threads:
-            opts = dict(bound="exp", B0=B0, B=B, grow=grow, threads=th, qid_base=1 << 41)
+            opts = dict(bound="exp", B0=B0, B=B, grow=grow, threads=th, qid_base=1 << 41, **extra)
             chosen = None
             for c in c_grid:
-                res = ds.adaptive(H, k, delta, 0, storage=storage, c_alpha=c, **opts)
+                res = ds.adaptive(H, k, delta, seed, storage=storage, c_alpha=c, **opts)
                 ri, rd = knn.rerank(ds.X, H, res["idx"], k)
                 if recall(ri, rd, ti, td) >= target + margin:
                     chosen = c
@@ -126,12 +129,12 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
                     break
             if chosen is None:
                 continue
-            res = ds.adaptive(H, k, delta, 0, storage=storage, c_alpha=chosen, **opts)  # untimed warm-up
+            res = ds.adaptive(H, k, delta, seed, storage=storage, c_alpha=chosen, **opts)  # untimed warm-up
             knn.rerank(ds.X, H, res["idx"], k)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(reps):
-                res = ds.adaptive(H, k, delta, 0, storage=storage, c_alpha=chosen, **opts)
+                res = ds.adaptive(H, k, delta, seed, storage=storage, c_alpha=chosen, **opts)
                 knn.rerank(ds.X, H, res["idx"], k)
             torch.cuda.synchronize()
             qps = reps * H.shape[0] / (time.perf_counter() - t0)
