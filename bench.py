@@ -483,12 +483,18 @@ def run_serve(args):
         n = max(4096, int(n * scale))
         X, P = synth.mixture_planted(n, m, SERVE["pool"], seed=100 + i)
         ds = knn.Dataset(torch.from_numpy(X).cuda(), copies=("bf16",))
+        extra = {}
+        if args.serve_shared:
+            ds.share(0, copies=("bf16",))
+            ds._shared_seed, ds._shared = 0, ("bf16",)
+            extra = dict(share_points=True, share_queries=True)
         t = runtime.autotune(ds, torch.from_numpy(P[:128]).cuda(), 10, 0.01, storage="bf16", target=RECALL_TARGET,
                              margin=0.0005, schedules=((8, 8, 1), (16, 16, 1)), threads=(512,), use_cache=False,
+                             c_grid=C_GRID + [1e-5, 3e-6], extra=extra,
                              cache=os.path.join(tempfile.gettempdir(), f"knn_serve_tune_{os.getpid()}.json"))
         b = t["best"]
         cfgs.append(serve.DatasetConfig(storage="bf16", c_alpha=b["c_alpha"], B0=b["B0"], B=b["B"], grow=b["grow"],
-                                        threads=b["threads"]))
+                                        threads=b["threads"], share=args.serve_shared))
         dss.append(ds)
         pools.append(P)
         tunes.append({"n": n, "d": m, **b})
@@ -524,6 +530,7 @@ def run_serve(args):
            "dtype": "bf16 gathers, f32 accumulation, f64 rerank", "data": "synthetic",
            "p50_ms": round(sat["p50_ms"], 3), "p99_ms": round(sat["p99_ms"], 3),
            "config": {"workload": SERVE["name"], "datasets": tunes, "scale": scale, "slots": args.serve_slots,
+                      "coordinates": "shared (masks 0)" if args.serve_shared else "per pair",
                       "mem_budget_gib": args.serve_mem, "seconds_of_arrivals": args.serve_seconds},
            "phases": phases, "recall_sample": round(hit / max(tot, 1), 6)}
     print(json.dumps(out), flush=True)
@@ -549,6 +556,8 @@ def main():
     ap.add_argument("--serve-scale", dest="serve_scale", type=float, default=1.0)
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
     ap.add_argument("--serve-mem", dest="serve_mem", type=int, default=24, help="GiB for in-flight round state")
+    ap.add_argument("--serve-per-pair", dest="serve_shared", action="store_false",
+                    help="draw coordinates per (query, point) pair instead of shared coordinates")
     args = ap.parse_args()
     if args.nq:
         WORKLOAD["nq"] = args.nq

@@ -65,6 +65,7 @@ class DatasetConfig:
     grow: int = 1
     threads: int = 512
     bound: str = "exp"
+    share: bool = False      # shared coordinates: both Philox masks zero, column-permuted copy
 
 
 class Server:
@@ -81,6 +82,10 @@ class Server:
         self.done: list[Request] = []
         self.launches = 0
         self.peak_mem = 0
+        for ds, c in zip(self.datasets, self.configs):
+            if c.share and not (getattr(ds, "_shared_seed", None) == seed and c.storage in getattr(ds, "_shared", ())):
+                ds.share(seed, copies=(c.storage,))
+                ds._shared_seed, ds._shared = seed, (c.storage,)
 
     # -- request flow
     def submit(self, req: Request):
@@ -90,7 +95,10 @@ class Server:
 
     def _opts(self, d):
         c = self.configs[d]
-        return dict(bound=c.bound, c_alpha=c.c_alpha, B0=c.B0, B=c.B, grow=c.grow, threads=c.threads)
+        o = dict(bound=c.bound, c_alpha=c.c_alpha, B0=c.B0, B=c.B, grow=c.grow, threads=c.threads)
+        if c.share:
+            o.update(share_points=True, share_queries=True)
+        return o
 
     def _state_bytes(self, d, nq, k_max):
         return self.datasets[d].multi_workspace_size(nq, k_max, **self._opts(d))

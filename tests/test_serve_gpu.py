@@ -111,3 +111,23 @@ def test_memory_budget_limits_what_is_in_flight(two_datasets):
     assert s.peak_mem <= 1.5 * one or s.launches == len(done)
     st = serve.latency_stats(done)
     assert st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_shared_coordinate_serving_same_alone_and_in_the_mix(two_datasets):
+    dss, pools, _ = two_datasets
+    cfg = [serve.DatasetConfig(storage="bf16", c_alpha=1e-3, share=True),
+           serve.DatasetConfig(storage="f32", c_alpha=1e-3, share=True)]
+    reqs = _requests(pools, 16, seed=13)
+    alone = {}
+    for r in reqs:
+        s = serve.Server(dss, cfg, slots=1, seed=4)
+        rr = _clone(r)
+        s.submit(rr)
+        s.drain()
+        alone[r.rid] = rr
+    s = serve.Server(dss, cfg, slots=3, max_batch=96, seed=4)
+    done = s.run([(0.0003 * i, _clone(r)) for i, r in enumerate(reqs)])
+    assert any(r.batch_size > r.Q.shape[0] for r in done)
+    for r in done:
+        a = alone[r.rid]
+        assert torch.equal(r.idx, a.idx) and torch.equal(r.dist, a.dist), r.rid
