@@ -68,7 +68,7 @@ typedef struct {
     uint64_t qid_base;  /* query i of the batch draws coordinates with query id qid_base + i */
     uint64_t mask_p;    /* point field mask of the Philox counter (all ones: independent draws) */
     uint64_t mask_q;    /* query field mask of the Philox counter (all ones: independent draws) */
-    int32_t threads;    /* threads per CTA of the round-loop kernel: 0 (default 512), 256 or 512 */
+    int32_t threads;    /* threads per query (CTA) of the round-loop kernel: 0 (default 512), 256, 512, 1024 */
     int32_t max_ctas;   /* cap on resident CTAs of the round-loop kernel (0: all that fit) */
 } knn_opts;
 

@@ -762,6 +762,62 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
   }
 }
 
+// Round 0 under shared coordinates: a point's first B0 draws are the first
+// B0 columns of its permuted row, so one thread per point reads them once and
+// forms the round-0 sum with every query of the chunk (their permuted values
+// staged in shared memory). The sum follows the round-loop kernel's order:
+// each block of 8 draws in sequence, then the two blocks added (the lane
+// butterfly for G = 2). Needs B0 <= 16.
+constexpr int kR0SharedThreads = 256;
+constexpr int kR0SharedQueries = 256;  // queries staged at a time
+
+template <class E>
+__global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, float* R0) {
+  __shared__ float qv[kR0SharedQueries * 16];
+  using Tp = typename E::T;
+  const int m = a.m;
+  const int64_t n = a.n;
+  const int B0 = a.B0;
+  const int64_t i = (int64_t)blockIdx.x * kR0SharedThreads + threadIdx.x;
+  float x[16];
+  if (i < n) {
+    const Tp* xr = static_cast<const Tp*>(a.G) + (size_t)i * (size_t)a.mp;
+    const float sc = E::kScaled ? __ldg(a.gscale + i) : 1.0f;
+    load8<E>(xr, x);
+    if (B0 > 8) load8<E>(xr + 8, x + 8);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) x[t] = E::kScaled ? __fmul_rn(x[t], sc) : x[t];
+  }
+  for (int q0 = 0; q0 < a.nq; q0 += kR0SharedQueries) {
+    const int qc = min(kR0SharedQueries, a.nq - q0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < qc * 16; e += kR0SharedThreads) {
+      const int qq = e >> 4, t = e & 15;
+      qv[e] = t < B0 ? __ldg(a.Q + (size_t)(q0 + qq) * m + a.jperm[t]) : 0.0f;
+    }
+    __syncthreads();
+    if (i < n) {
+      for (int qq = 0; qq < qc; ++qq) {
+        const float* v = qv + qq * 16;
+        float p0 = 0.0f, p1 = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+          if (w < B0) {
+            const float d = x[w] - v[w];
+            p0 = fmaf(d, d, p0);
+          }
+#pragma unroll
+        for (int w = 8; w < 16; ++w)
+          if (w < B0) {
+            const float d = x[w] - v[w];
+            p1 = fmaf(d, d, p1);
+          }
+        R0[(size_t)(q0 + qq) * (size_t)n + i] = B0 > 8 ? p0 + p1 : p0;
+      }
+    }
+  }
+}
+
 // Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and
 // xr[2] = 1 if any element is NaN or infinite.
 static __global__ void minmax_kernel(const float* __restrict__ X, size_t count, uint32_t* xr) {
@@ -808,12 +864,13 @@ struct AdaptivePlan {
   size_t smem = 0;
 };
 
-// The round-loop kernel instantiated for a thread count (512 or 256; both
-// keep 64 registers per thread, 32 or 16 warps per query).
+// The round-loop kernel instantiated for a thread count (256, 512 or 1024;
+// all keep 64 registers per thread: 8, 16 or 32 warps per query).
 template <class E>
 static void* rounds_kernel_for(int threads) {
-  return threads == 256 ? reinterpret_cast<void*>(adaptive_rounds_kernel<256, E>)
-                        : reinterpret_cast<void*>(adaptive_rounds_kernel<512, E>);
+  if (threads == 256) return reinterpret_cast<void*>(adaptive_rounds_kernel<256, E>);
+  if (threads == 1024) return reinterpret_cast<void*>(adaptive_rounds_kernel<1024, E>);
+  return reinterpret_cast<void*>(adaptive_rounds_kernel<512, E>);
 }
 
 template <class E>
@@ -821,7 +878,7 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   DeviceInfo di;
   knn_status s = device_info(&di);
   if (s != KNN_OK) return s;
-  p->threads = (o && o->threads == 256) ? 256 : kAdaptiveNT;
+  p->threads = (o && (o->threads == 256 || o->threads == 1024)) ? o->threads : kAdaptiveNT;
   p->smem = adaptive_smem_bytes(m, E::kPerm);
   const void* fn = rounds_kernel_for<E>(p->threads);
   s = cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
@@ -849,6 +906,8 @@ template <class E>
 static knn_status launch_rounds(const AdaptivePlan& p, const AdaptiveArgs& a, cudaStream_t stream) {
   if (p.threads == 256)
     adaptive_rounds_kernel<256, E><<<p.grid, 256, p.smem, stream>>>(a);
+  else if (p.threads == 1024)
+    adaptive_rounds_kernel<1024, E><<<p.grid, 1024, p.smem, stream>>>(a);
   else
     adaptive_rounds_kernel<512, E><<<p.grid, 512, p.smem, stream>>>(a);
   return cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
@@ -906,8 +965,8 @@ static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double d
     return set_error("footnote bound needs delta/n < 1/e"), KNN_EINVAL;
   if (o.bound == KNN_BOUND_EXP && !(o.c_alpha > 0.0)) return set_error("c_alpha must be > 0"), KNN_EINVAL;
   if (o.B0 < 1 || o.B < 1) return set_error("B0 and B must be >= 1"), KNN_EINVAL;
-  if (o.threads != 0 && o.threads != 256 && o.threads != 512)
-    return set_error("threads must be 0, 256 or 512"), KNN_EINVAL;
+  if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
+    return set_error("threads must be 0, 256, 512 or 1024"), KNN_EINVAL;
   if (o.grow != 0 && o.grow != 1) return set_error("grow must be 0 or 1"), KNN_EINVAL;
   return KNN_OK;
 }

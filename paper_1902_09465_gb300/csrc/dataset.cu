@@ -187,7 +187,8 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
                                      const MixedBatch* mix = nullptr) {
   const int64_t n = ds->n;
   const int32_t m = ds->m;
-  const bool r0 = !E::kPerm && round0_applies(m, o);
+  // round 0 point-major: the shared form for B0 <= 16, the staged-rows pass otherwise
+  const bool r0 = E::kPerm ? (o.B0 < m && o.B0 <= 16) : round0_applies(m, o);
   const int chunk = r0 ? round0_chunk(n, nq) : nq;
   AdaptivePlan p;
   knn_status s = plan_adaptive<E>(n, m, chunk, k, &o, &p);
@@ -263,7 +264,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.jperm = ds->jperm;
   a.mp = ds->mp;
   const int rows = round0_rows(m);
-  if (r0) {
+  if (r0 && !E::kPerm) {
     s = cuda_check(cudaFuncSetAttribute(round0_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)((size_t)rows * m * 4)),
                    "cudaFuncSetAttribute(round0)");
@@ -289,9 +290,15 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
     ac.qid_base = a.qid_base + (uint64_t)q0;
     s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
     if (s == KNN_OK && r0) {
-      const unsigned blocks = (unsigned)((n + rows - 1) / rows);
-      round0_kernel<E><<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf);
-      s = cuda_check(cudaGetLastError(), "round0_kernel launch");
+      if constexpr (E::kPerm) {
+        const unsigned blocks = (unsigned)((n + kR0SharedThreads - 1) / kR0SharedThreads);
+        round0_shared_kernel<E><<<blocks, kR0SharedThreads, 0, stream>>>(ac, r0buf);
+        s = cuda_check(cudaGetLastError(), "round0_shared_kernel launch");
+      } else {
+        const unsigned blocks = (unsigned)((n + rows - 1) / rows);
+        round0_kernel<E><<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf);
+        s = cuda_check(cudaGetLastError(), "round0_kernel launch");
+      }
     }
     if (s == KNN_OK) s = launch_rounds<E>(p, ac, stream);
   }

@@ -93,7 +93,7 @@ def tune_key(ds: knn.Dataset, k: int, storage: str) -> str:
 
 
 def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, storage: str = "f32",
-             target: float = 0.999, margin: float = 0.0005, schedules=DEFAULT_SCHEDULES, threads=(512, 256),
+             target: float = 0.999, margin: float = 0.0005, schedules=DEFAULT_SCHEDULES, threads=(512, 1024),
              c_grid=DEFAULT_C_GRID, reps: int = 3, cache: str | None = None, use_cache: bool = True,
              seed: int = 0, extra=None):
     """Picks (B0, B, grow, threads, C_alpha) for a dataset: for every

@@ -22,12 +22,13 @@ def data():
     ds.close()
 
 
-def test_threads_256_and_512_give_identical_results(data):
+def test_thread_counts_give_identical_results(data):
     ds, Qd = data
     a = ds.adaptive(Qd, 10, 0.01, 3, bound="exp", c_alpha=1e-3, grow=1, threads=512, trace=True)
-    b = ds.adaptive(Qd, 10, 0.01, 3, bound="exp", c_alpha=1e-3, grow=1, threads=256, trace=True)
-    for key in a:
-        assert torch.equal(a[key], b[key]), key
+    for th in (256, 1024):
+        b = ds.adaptive(Qd, 10, 0.01, 3, bound="exp", c_alpha=1e-3, grow=1, threads=th, trace=True)
+        for key in a:
+            assert torch.equal(a[key], b[key]), (th, key)
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])

@@ -13,11 +13,11 @@ pytestmark = pytest.mark.gpu
 SH = dict(share_points=True, share_queries=True)
 
 
-@pytest.mark.parametrize("m", [784, 77, 5])
-def test_shared_copies_equal_per_pair_draws(m):
+@pytest.mark.parametrize("m,B0", [(784, 8), (784, 16), (77, 12), (5, 3), (300, 32)])
+def test_shared_copies_equal_per_pair_draws(m, B0):
     X, Q = synth.pixel_mixture(12000, m, 24, seed=m)
     Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
-    opt = dict(bound="exp", c_alpha=1e-3, B0=8, B=8, grow=1, **SH)
+    opt = dict(bound="exp", c_alpha=1e-3, B0=B0, B=8, grow=1, **SH)
     with knn.Dataset(Xd, copies=("bf16", "fp8")) as ds:
         before = {st: ds.adaptive(Qd, 10, 0.01, 42, storage=st, trace=True, **opt) for st in ("f32", "bf16", "fp8")}
         ds.share(42, copies=("f32", "bf16", "fp8"))
