@@ -489,7 +489,7 @@ def run_serve(args):
             ds._shared_seed, ds._shared = 0, ("bf16",)
             extra = dict(share_points=True, share_queries=True)
         t = runtime.autotune(ds, torch.from_numpy(P[:128]).cuda(), 10, 0.01, storage="bf16", target=RECALL_TARGET,
-                             margin=0.0005, schedules=((8, 8, 1), (16, 16, 1)), threads=(512,), use_cache=False,
+                             margin=0.0005, schedules=((8, 8, 1), (16, 16, 1)), threads=(512, 1024), use_cache=False,
                              c_grid=C_GRID + [1e-5, 3e-6], extra=extra,
                              cache=os.path.join(tempfile.gettempdir(), f"knn_serve_tune_{os.getpid()}.json"))
         b = t["best"]

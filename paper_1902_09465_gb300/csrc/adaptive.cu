@@ -30,7 +30,8 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
   if (plan_adaptive<ElemF32>(n, m, nq, k, &o, &p) != KNN_OK) return 0;
   Carve cv;
   carve_adaptive(cv, n, p, nullptr);
-  if (round0_applies(m, o)) cv.take<float>((size_t)round0_chunk(n, nq) * (size_t)n);  // dataset path only
+  if (round0_applies(m, o) || (o.B0 < m && o.B0 <= 16))  // dataset paths only
+    cv.take<float>((size_t)round0_chunk(n, nq, p.grid) * (size_t)n);
   return cv.off + 256;
 }
 

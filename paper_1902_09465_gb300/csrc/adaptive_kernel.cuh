@@ -948,8 +948,10 @@ constexpr size_t kR0BufferBytes = size_t(1) << 30;
 
 static inline bool round0_applies(int32_t m, const knn_opts& o) { return o.B0 < m && o.B0 <= 256; }
 
-static inline int round0_chunk(int64_t n, int32_t nq) {
-  const int64_t c = (int64_t)(kR0BufferBytes / (4 * (size_t)n));
+// Queries per chunk: as many as the buffer holds, but never fewer than the
+// round-loop kernel's resident CTAs (a smaller chunk would leave SMs idle).
+static inline int round0_chunk(int64_t n, int32_t nq, int grid) {
+  const int64_t c = std::max<int64_t>((int64_t)(kR0BufferBytes / (4 * (size_t)n)), grid);
   return (int)std::max<int64_t>(1, std::min<int64_t>(nq, c));
 }
 

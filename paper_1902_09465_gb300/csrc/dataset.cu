@@ -189,10 +189,10 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   const int32_t m = ds->m;
   // round 0 point-major: the shared form for B0 <= 16, the staged-rows pass otherwise
   const bool r0 = E::kPerm ? (o.B0 < m && o.B0 <= 16) : round0_applies(m, o);
-  const int chunk = r0 ? round0_chunk(n, nq) : nq;
   AdaptivePlan p;
-  knn_status s = plan_adaptive<E>(n, m, chunk, k, &o, &p);
+  knn_status s = plan_adaptive<E>(n, m, nq, k, &o, &p);
   if (s != KNN_OK) return s;
+  const int chunk = r0 ? round0_chunk(n, nq, p.grid) : nq;
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
   if (r0) measure.take<float>((size_t)chunk * (size_t)n);
