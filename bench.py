@@ -44,12 +44,14 @@ METRIC = "k-NN queries/s at recall>=0.999 (adaptive, FP32, +FP64 rerank)"
 C_GRID = [1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5]
 RECALL_TARGET = 0.999
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the round-loop kernel on this workload, taken from one ncu capture. It is
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one adaptive
+# call on this workload (round-0 kernel + round-loop kernel), from one ncu
+# capture of the timed configuration. It is
 # reported only while the kernel sources hash to the recorded value and the
 # launch configuration matches; otherwise the roofline's traffic is null.
-TRAFFIC_CAPTURE = {"sha1": "70c8f89578b58e196ea7eacf9ec167196f6a09b6", "bytes": 36960927488 + 831840000,
-                   "config": {"c_alpha": 3e-4, "B0": 16, "B": 16, "grow": 1, "threads": 512, "nq": 1024}}
+TRAFFIC_CAPTURE = {"sha1": "b8740c1f54b6308c074f407437a0da6ec4ce60ef",
+                   "bytes": (318e6 + 355e6) + (21.06e9 + 1.11e9),
+                   "config": {"c_alpha": 1e-3, "B0": 8, "B": 8, "grow": 1, "threads": 1024, "nq": 1024}}
 
 
 def kernel_sources_sha1():
