@@ -259,6 +259,12 @@ def run_ours(args, rank, world, local_rank):
     # writes the round-0 sums) and the round-loop kernel (reads those sums,
     # then 4 B per later coordinate evaluation, and the query rows).
     r0_evals = nq * n * B0 if B0 < m else 0
+    # kernels of one graph replay: per query chunk (the round-0 sums of a chunk
+    # fit a 1 GiB buffer, a chunk never smaller than the resident grid) the
+    # round-0 kernel and the round loop, then the rerank
+    grid = torch.cuda.get_device_properties(dev).multi_processor_count * (1024 // best["threads"])
+    chunk = min(nq, max((1 << 30) // (4 * n), grid)) if r0_evals else nq
+    launches_per_step = -(-nq // chunk) * (2 if r0_evals else 1) + 1
     alg_bytes = (4 * n * m + 2 * 4 * nq * n if r0_evals else 0) + 4 * (evals - r0_evals) + 4 * nq * m
     hbm, peak_kind = peaks()
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
@@ -402,7 +408,8 @@ def run_ours(args, rank, world, local_rank):
                                                "ms_per_batch": round(exact_simt_ms, 4)}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 5), "traffic": traffic,
-                     "kernel": "knn_adaptive_ds call = round0_kernel<ElemF32> + adaptive_rounds_kernel<512, ElemF32>",
+                     "kernel": f"knn_adaptive_ds call = round0_kernel<ElemF32> + adaptive_rounds_kernel<{best['threads']}, "
+                               "ElemF32>",
                      "kernel_ms": round(kern_ms, 4),
                      "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
                      "sector_gbs": round(sector_gbs, 2),
@@ -411,7 +418,7 @@ def run_ours(args, rank, world, local_rank):
                              "granule a random 4-byte gather moves)"},
         "e2e": {"value": round(world * nq / (e2e_ms / 1e3), 3), "unit": "queries/s",
                 "h2d_bytes_per_step": nq * m * 4, "d2h_bytes_per_step": nq * k * 16},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
     }
     return result

@@ -44,7 +44,7 @@ class AdaptiveParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double),
                 ("delta", C.c_double), ("B0", C.c_int32), ("B", C.c_int32), ("grow", C.c_int32),
                 ("seed", C.c_uint64), ("qid", C.c_uint64), ("mask_p", C.c_uint64), ("mask_q", C.c_uint64),
-                ("tol", C.c_double), ("storage", C.c_int32)]
+                ("tol", C.c_double), ("storage", C.c_int32), ("block", C.c_int32)]
 
 
 class AdaptiveStats(C.Structure):
@@ -135,12 +135,15 @@ def exact_knn(X, Q, k, threads=0):
 
 
 def make_params(k, h=None, delta=0.01, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, seed=0,
-                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32"):
+                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32", block=1):
+    """Parameters of the batched rounds; `block` = coordinates per sample
+    (1: single coordinates as in the paper; g > 1: blocks of g consecutive
+    coordinates, B0 and B then count blocks)."""
     full = (1 << 64) - 1
     return AdaptiveParams(int(k), int(k if h is None else h), BOUND[bound] if isinstance(bound, str) else int(bound),
                           float(c_alpha), float(delta), int(B0), int(B), int(grow), int(seed), int(qid),
                           0 if share_points else full, 0 if share_queries else full, float(tol),
-                          STORAGE[storage] if isinstance(storage, str) else int(storage))
+                          STORAGE[storage] if isinstance(storage, str) else int(storage), int(block))
 
 
 def adaptive(X, Q, params: AdaptiveParams, replay=None, want_state=True, threads=0):

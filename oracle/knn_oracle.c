@@ -20,6 +20,14 @@
  *     form of the LUCB indices (Eq. d_ind) and of the termination argument
  *     (Eq. termination and the first paragraph of the proof of Theorem 1).
  *   - sequential: Algorithm 1 as printed (two arms per iteration).
+ *   - block samples (not in the paper): with block g > 1 a sample is one of
+ *     M = ceil(m/g) blocks of g consecutive coordinates, drawn uniformly with
+ *     replacement, and its value the block's sum of squared differences. The
+ *     block sum over g (times 1/span^2) lies in [0, 1], so the sampled
+ *     estimator of Section 4 and its bounds apply with u = blocks drawn; its
+ *     mean over all M blocks is d^2/(M g), the same for every point up to the
+ *     factor d^2, and after M samples the estimate is exact (Algorithm 1's
+ *     cap at T = m, with M in place of m).
  */
 #include "knn_oracle.h"
 
@@ -240,8 +248,12 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
                              orc_adaptive_stats* st) {
     const int32_t k = p->k, h = p->h;
     const int64_t kh = (int64_t)k + h;
-    if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->B0 < 1 || p->B < 1)
+    if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->B0 < 1 || p->B < 1 ||
+        p->block < 0)
         return 1;
+    /* g coordinates per sample, M samples make the exact distance */
+    const int32_t g = p->block > 1 ? p->block : 1;
+    const int32_t M = (int32_t)(((int64_t)m + g - 1) / g);
     memset(st, 0, sizeof(*st));
     for (int64_t t = 0; t < kh; ++t) out_idx[t] = -1;
 
@@ -299,11 +311,12 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
     int32_t r = 0, term = 0;
     for (;;) {
         int64_t Br = round_samples(p, r, Tcur);
-        int exact = (Tcur + Br >= m);
-        int64_t Tn = exact ? m : Tcur + Br;
+        int exact = (Tcur + Br >= M);
+        int64_t Tn = exact ? M : Tcur + Br;
         /* Sample step (Algorithm 1 update, batched): every active point
          * gets draws Tcur .. Tn-1, or its exact distance when the count
-         * would reach m ("If T = m, compute the distance exactly"). */
+         * would reach M (Algorithm 1 computes the distance exactly once all
+         * m coordinates would be sampled; M = m for single coordinates). */
         for (int64_t i = 0; i < n; ++i) {
             if (status[i] != ORC_ACTIVE) continue;
             const float* xi = G + (size_t)i * (size_t)m;
@@ -311,22 +324,28 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
                 Sx[i] = sqdist(X + (size_t)i * (size_t)m, q, m);
             } else {
                 for (int64_t t = Tcur; t < Tn; ++t) {
-                    int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, m, p->mask_p, p->mask_q);
-                    double d = (double)xi[j] - (double)q[j];
-                    Sx[i] += d * d;
+                    /* draw t picks block b: coordinates b*g .. min(b*g + g, m) - 1 */
+                    int32_t b = orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, M, p->mask_p, p->mask_q);
+                    int32_t j1 = (b + 1) * g < m ? (b + 1) * g : m;
+                    for (int32_t j = b * g; j < j1; ++j) {
+                        double d = (double)xi[j] - (double)q[j];
+                        Sx[i] += d * d;
+                    }
                 }
             }
             Tx[i] = (int32_t)Tn;
         }
-        evals += nact * (exact ? (int64_t)m : Br);
+        evals += nact * (exact ? (int64_t)m : Br * g);
         const double w = exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta) + eps;
+        /* estimate: mean per coordinate of the sampled blocks (S / (T g)) */
+        const double Tg = (double)Tn * (double)g;
 
         /* Bounds of the non-eliminated points: current ones for active
          * points, frozen ones for accepted points. */
         int64_t cnt = 0;
         for (int64_t i = 0; i < n; ++i) {
             if (status[i] == ORC_ACTIVE) {
-                double d = Sx[i] / (double)Tn;
+                double d = Sx[i] / Tg;
                 su[cnt].v = d + w; su[cnt].mag = d + w;
                 sl[cnt].v = d - w; sl[cnt].mag = d + w;
                 ++cnt;
@@ -352,7 +371,7 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
         for (int64_t i = 0; i < n; ++i) {
             newst[i] = status[i];
             if (status[i] != ORC_ACTIVE) continue;
-            double d = Sx[i] / (double)Tn;
+            double d = Sx[i] / Tg;
             double U = d + w, L = d - w, mag = d + w;
             int o = (L > tauU) ? ORC_ELIMINATED : ((U < tauL) ? ORC_ACCEPTED : ORC_ACTIVE);
             if (replay) {
@@ -396,7 +415,7 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
         ++r;
     }
     for (int64_t i = 0; i < n; ++i)
-        if (status[i] == ORC_ACTIVE) { cx[i] = 4 * r + ORC_ACTIVE; dh[i] = Sx[i] / (double)Tx[i]; }
+        if (status[i] == ORC_ACTIVE) { cx[i] = 4 * r + ORC_ACTIVE; dh[i] = Sx[i] / ((double)Tx[i] * g); }
     if (replay)
         for (int64_t i = 0; i < n; ++i)
             if ((replay[i] >> 2) > r || ((replay[i] & 3) == ORC_ACTIVE && (replay[i] >> 2) != r))

@@ -50,6 +50,9 @@ typedef struct {
     uint64_t seed, qid, mask_p, mask_q;
     double tol;           /* relative width of the near-threshold band used in replay */
     int32_t storage;      /* ORC_STORE_*: the values the samples are taken from */
+    int32_t block;        /* coordinates per sample: 0 or 1 is the paper's one coordinate; g > 1 draws
+                           * one of ceil(m/g) blocks of g consecutive coordinates (the last may be
+                           * shorter) and adds the block's sum of squared differences */
 } orc_adaptive_params;
 
 /* Storage of the gathered copy: FP32 itself, BF16 (round to nearest even),
@@ -64,7 +67,7 @@ float orc_round_bf16(float x);
 float orc_round_e4m3(float x);
 
 typedef struct {
-    int64_t evals;        /* coordinate evaluations: samples drawn + m per exact distance */
+    int64_t evals;        /* coordinate evaluations: samples drawn x block + m per exact distance */
     int32_t rounds;
     int32_t count;        /* candidates returned (<= k+h) */
     int32_t term;         /* 1: size <= k+h; 2: >= k accepted; 3: exact round; 0: n <= k+h */
@@ -76,7 +79,8 @@ typedef struct {
 
 /* Batched adaptive rounds for one query (hot-path rules, see knn_oracle.c).
  * Outputs: out_idx[k+h] (-1 padded), code[n] (4*round + kind), S[n] (sum of
- * sampled squared differences, or the exact squared distance), T[n] (samples).
+ * sampled squared differences, or the exact squared distance), T[n] (samples;
+ * blocks with block > 1, ceil(m/block) once exact).
  * If `replay` is non-NULL it holds another implementation's codes for the
  * same query; the oracle then adopts that decision wherever the two disagree
  * and counts the disagreement as near-band or mismatch. */
