@@ -70,6 +70,15 @@ typedef struct {
     uint64_t mask_q;    /* query field mask of the Philox counter (all ones: independent draws) */
     int32_t threads;    /* threads per query (CTA) of the round-loop kernel: 0 (default 512), 256, 512, 1024 */
     int32_t max_ctas;   /* cap on resident CTAs of the round-loop kernel (0: all that fit) */
+    int32_t block;      /* coordinates per sample, 0..64. 0 or 1: single coordinates (the paper's
+                         * estimator). g > 1: block samples (not in the paper): a draw picks one of
+                         * M = ceil(m/g) blocks of g consecutive coordinates (the last may be
+                         * shorter), uniformly with replacement, and adds the block's sum of
+                         * squared differences; B0 and B count blocks, the estimate is
+                         * S / (T g), alpha takes u = T blocks (a block sum over g lies in
+                         * [0, span^2], so the bounds of Section 4 hold), the distance is exact
+                         * once T + B_r >= M, and out_evals counts g per block drawn. With
+                         * g x element size = 32 bytes a draw reads one DRAM sector. */
 } knn_opts;
 
 void knn_opts_default(knn_opts* opts);
@@ -100,7 +109,7 @@ size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, 
  * delta:    in (0,1); FOOTNOTE additionally needs delta/n < 1/e.
  * out_idx:  nq x (k+h) int64, -1 padded (device, required).
  * out_count:nq int32 candidates returned (device, required).
- * out_evals:nq int64 coordinate evaluations: samples drawn + m per exact
+ * out_evals:nq int64 coordinate evaluations: samples drawn (x block) + m per exact
  *           distance (device, required).
  * out_rounds: nq int32 rounds run (device, may be NULL).
  * log_code: nq x n int32 decision log, 4*round + kind (kind 0 still active at
@@ -139,6 +148,7 @@ knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const float* Q, in
  *   must start fresh. Calls whose work overlaps on the GPU (on different
  *   streams or from different threads without ordering) race on the array
  *   and give wrong results; order them on one stream.
+ * - Single coordinates only: opts->block above 1 returns KNN_EINVAL.
  */
 size_t knn_adaptive_noalloc_scratch_bytes(void);
 knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,

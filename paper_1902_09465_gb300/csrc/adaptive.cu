@@ -22,15 +22,18 @@ extern "C" void knn_opts_default(knn_opts* o) {
   o->mask_q = ~0ULL;
   o->threads = 0;
   o->max_ctas = 0;
+  o->block = 1;
 }
 
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {
   const knn_opts o = resolve(opts, k);
   AdaptivePlan p;
-  if (plan_adaptive<ElemF32>(n, m, nq, k, &o, &p) != KNN_OK) return 0;
+  const knn_status ps = o.block > 1 ? plan_adaptive<Blk<ElemF32>>(n, m, nq, k, &o, &p)
+                                    : plan_adaptive<ElemF32>(n, m, nq, k, &o, &p);
+  if (ps != KNN_OK) return 0;
   Carve cv;
   carve_adaptive(cv, n, p, nullptr);
-  if (round0_applies(m, o) || (o.B0 < m && o.B0 <= 16))  // dataset paths only
+  if (round0_applies(m, o) || (o.block <= 1 && o.B0 < m && o.B0 <= 16))  // dataset paths only
     cv.take<float>((size_t)round0_chunk(n, nq, p.grid) * (size_t)n);
   return cv.off + 256;
 }
@@ -50,7 +53,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   }
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   AdaptivePlan p;
-  s = plan_adaptive<ElemF32>(n, m, nq, k, &o, &p);
+  s = o.block > 1 ? plan_adaptive<Blk<ElemF32>>(n, m, nq, k, &o, &p) : plan_adaptive<ElemF32>(n, m, nq, k, &o, &p);
   if (s != KNN_OK) return s;
   Carve measure;
   const size_t need = carve_adaptive(measure, n, p, nullptr) + 256;
@@ -137,7 +140,13 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
-  s = launch_rounds<ElemF32>(p, a, stream);
+  if (o.block > 1) {
+    set_blocks<Blk<ElemF32>>(a, o);
+    s = launch_rounds<Blk<ElemF32>>(p, a, stream);
+  } else {
+    set_blocks<ElemF32>(a, o);
+    s = launch_rounds<ElemF32>(p, a, stream);
+  }
   ws.release();
   return s;
 }
@@ -188,6 +197,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   const knn_opts o = resolve(opts, k);
   knn_status s = validate(n, m, nq, k, delta, o);
   if (s != KNN_OK) return s;
+  if (o.block > 1) return set_error("knn_adaptive_noalloc takes single coordinates (block 0 or 1)"), KNN_EINVAL;
   if (nq == 0) return KNN_OK;
   if (!X || !Q || !out_idx || !out_count || !out_evals) {
     set_error("X, Q, out_idx, out_count and out_evals are required");
@@ -286,5 +296,6 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  set_blocks<ElemF32>(a, o);
   return launch_rounds<ElemF32>(p, a, stream);
 }

@@ -70,6 +70,9 @@ struct AdaptiveArgs {
   int32_t* log_code;
   float* log_S;
   int32_t vec;  // rows of X start on 16-byte boundaries: exact rows use 16-byte loads
+  int32_t g;    // coordinates per sample (1: single coordinates; > 1: blocks of g consecutive ones)
+  int32_t Mb;   // samples that make a distance exact: ceil(m / g)
+  int32_t gvec; // a block is 32 bytes of the copy on 16-byte aligned rows: two 16-byte loads
   const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
   const int32_t* jperm; // shared-coordinate copies: column of draw t (t < m), for Perm element types
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
@@ -85,6 +88,7 @@ struct ElemF32 {
   static constexpr int kStorage = KNN_STORE_F32;
   static constexpr bool kScaled = false;
   static constexpr bool kPerm = false;
+  static constexpr bool kBlk = false;
   __device__ static __forceinline__ float load(const T* p) { return __ldg(p); }
   __device__ static __forceinline__ float conv(T v) { return v; }
 };
@@ -93,6 +97,7 @@ struct ElemBF16 {
   static constexpr int kStorage = KNN_STORE_BF16;
   static constexpr bool kScaled = false;
   static constexpr bool kPerm = false;
+  static constexpr bool kBlk = false;
   __device__ static __forceinline__ float conv(T v) { return __uint_as_float((uint32_t)v << 16); }
   __device__ static __forceinline__ float load(const T* p) { return conv(__ldg(p)); }
 };
@@ -101,6 +106,7 @@ struct ElemFP8 {
   static constexpr int kStorage = KNN_STORE_FP8;
   static constexpr bool kScaled = true;
   static constexpr bool kPerm = false;
+  static constexpr bool kBlk = false;
   __device__ static __forceinline__ float conv(T v) {
     __nv_fp8_e4m3 f;
     f.__x = v;
@@ -128,6 +134,13 @@ struct AdaptiveShared {
 template <class Base>
 struct Perm : Base {
   static constexpr bool kPerm = true;
+};
+
+// Block samples (g > 1 coordinates per draw) over a stored copy: the same
+// round loop with gather_blocks in place of gather_sampled.
+template <class Base>
+struct Blk : Base {
+  static constexpr bool kBlk = true;
 };
 
 // 8 consecutive elements of a shared-coordinate row (16-byte aligned blocks
@@ -348,6 +361,133 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
   }
 }
 
+// Sum of squared differences over one 32-byte block of the copy (two 16-byte
+// words, elements in memory order) against the FP32 query values qb, added
+// to part in coordinate order.
+template <class E>
+__device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, const float* qb, float sc, float part) {
+  constexpr int per = 4 / (int)sizeof(typename E::T);  // elements per 32-bit word
+  const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+  for (int c4 = 0; c4 < 8 * per; c4 += 4) {
+    const float4 q4 = *reinterpret_cast<const float4*>(qb + c4);
+    const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = c4 + e;
+      const uint32_t word = wv[c / per];
+      float x;
+      if constexpr (per == 1)
+        x = __uint_as_float(word);
+      else if constexpr (per == 2)
+        x = E::conv((typename E::T)(word >> (16 * (c & 1))));
+      else
+        x = E::conv((typename E::T)(word >> (8 * (c & 3))));
+      if constexpr (E::kScaled) x = __fmul_rn(x, sc);
+      const float d = x - qv[e];
+      part = fmaf(d, d, part);
+    }
+  }
+  return part;
+}
+
+// Block samples (g > 1 coordinates per draw): draw s of a pair picks block
+// jb = floor(word_s * Mb / 2^32) and adds the squared differences of its
+// coordinates jb*g .. min(jb*g + g, m) - 1 in order. Lanes, items (one
+// Philox block of 8 draws) and the reduction are those of gather_sampled. A
+// 32-byte block on 16-byte aligned rows (gvec) is two 16-byte loads, F draws
+// in flight per lane; a ragged last block is read element by element.
+template <int NT, class E>
+__device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
+                                              const float* qs, const int32_t* idc, float* Sc, float* Cc,
+                                              uint32_t* hist) {
+  using Tp = typename E::T;
+  constexpr int F = 2;
+  const int m = a.m, g = a.g;
+  const uint32_t Mb = (uint32_t)a.Mb;
+  const uint64_t blo = (uint64_t)T >> 3, bhi = (uint64_t)(Tn - 1) >> 3;
+  const int nblk = (int)(bhi - blo + 1);
+  int G = 1;
+  while (G < nblk && G < 32) G <<= 1;
+  const int lg = __ffs(G) - 1;
+  const int nbl = (nblk + G - 1) / G;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int grp = lane >> lg, gl = lane & (G - 1);
+  const int ppw = 32 >> lg;
+  const int pstride = (NT / 32) * ppw;
+  const uint64_t qfield = qid & a.mask_q;
+  const Tp* G0 = static_cast<const Tp*>(a.G);
+  const int first = warp * ppw;
+  const int npairs = first < nact ? (nact - first + pstride - 1) / pstride : 0;  // warp-uniform
+  const int nitems = npairs * nbl;
+  float part = 0.0f;
+  for (int t = 0; t < nitems; ++t) {
+    const int pi = t / nbl, jt = t - pi * nbl;
+    const int sidx = first + grp + pi * pstride;
+    const uint64_t b = blo + (uint64_t)(gl + jt * G);
+    if (sidx < nact && b <= bhi) {
+      const int id = (r == 0) ? sidx : idc[sidx];
+      const Philox4x64 ph = philox4x64_10(b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0);
+      const Tp* xr = G0 + (size_t)id * (size_t)m;
+      const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
+      const int64_t s0 = (int64_t)(b << 3);
+#pragma unroll
+      for (int w0 = 0; w0 < 8; w0 += F) {
+        uint4 v[F][2];
+        int cb[F];
+        bool ok[F], full[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          const int64_t s = s0 + w0 + f;
+          ok[f] = s >= T && s < Tn;
+          cb[f] = (int)__umulhi(philox_word(ph, w0 + f), Mb) * g;
+          full[f] = a.gvec && cb[f] + g <= m;
+          if (ok[f] && full[f]) {
+            const uint4* p = reinterpret_cast<const uint4*>(xr + cb[f]);
+            v[f][0] = __ldg(p);
+            v[f][1] = __ldg(p + 1);
+          }
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          if (!ok[f]) continue;
+          if (full[f]) {
+            part = block_sum32<E>(v[f][0], v[f][1], qs + cb[f], sc, part);
+          } else {
+            const int c1 = min(cb[f] + g, m);
+            for (int c = cb[f]; c < c1; ++c) {
+              float x = E::load(xr + c);
+              if (E::kScaled) x = __fmul_rn(x, sc);
+              const float d = x - qs[c];
+              part = fmaf(d, d, part);
+            }
+          }
+        }
+      }
+    }
+    if ((t + 1) % nbl == 0) {  // last block of this point: combine the G lanes and store
+#pragma unroll
+      for (int o = 16; o; o >>= 1)
+        if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (sidx < nact && gl == 0) {
+        float S;
+        if (r == 0) {
+          S = part;
+        } else {
+          const float S0 = Sc[sidx], c0 = Cc[sidx];
+          const float y = part - c0;
+          const float tt = S0 + y;
+          Cc[sidx] = (tt - S0) - y;
+          S = tt;
+        }
+        Sc[sidx] = S;
+        atomicAdd(&hist[f2key(S) >> 20], 1u);
+      }
+      part = 0.0f;
+    }
+  }
+}
+
 // Exact round: one warp per active point, the full FP32 row of the data
 // (16-byte loads when rows are 16-byte aligned).
 template <int NT>
@@ -495,8 +635,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     float min_elim = INFINITY;
     for (;;) {
       const int64_t Br = (r == 0) ? a.B0 : (a.grow ? (T > a.B ? T : (int64_t)a.B) : (int64_t)a.B);
-      const bool exact = T + Br >= m;
-      const int64_t Tn = exact ? m : T + Br;
+      const bool exact = T + Br >= a.Mb;  // Mb = m for single coordinates
+      const int64_t Tn = exact ? a.Mb : T + Br;
       const int32_t* idc = ids0 + (size_t)cur * n;
       const bool pre = (r == 0) && a.R0 && !exact;  // round-0 sums computed point-major beforehand
       float* Sc = pre ? const_cast<float*>(a.R0) + (size_t)q * (size_t)n : S0 + (size_t)cur * n;
@@ -507,12 +647,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
       else if (pre)
         for (int i = tid; i < nact; i += NT) atomicAdd(&hist[f2key(Sc[i]) >> 20], 1u);
+      else if constexpr (E::kBlk)
+        gather_blocks<NT, E>(a, qid, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
       else
         gather_sampled<NT, E>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
-      evals += (int64_t)nact * (exact ? (int64_t)m : Br);
+      evals += (int64_t)nact * (exact ? (int64_t)m : Br * a.g);
       const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
-      const float Tf = (float)Tn;
+      const float Tf = (float)(Tn * a.g);  // estimate = S / (T g): mean per coordinate
 
       // ---- thresholds
       const int kk = min(k + 1, nact);
@@ -745,12 +887,25 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
         const uint64_t id = (uint64_t)(p0 + pi);
         const Philox4x64 ph = philox4x64_10((uint64_t)gl, id & a.mask_p, qfield, 0, a.seed, 0);
         const float* xr = rows + (size_t)pi * m;
+        if constexpr (!E::kBlk) {
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          if (gl * 8 + w < a.B0) {
-            const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
-            const float d = xr[j] - __ldg(qr + j);
-            part = fmaf(d, d, part);
+          for (int w = 0; w < 8; ++w) {
+            if (gl * 8 + w < a.B0) {
+              const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+              const float d = xr[j] - __ldg(qr + j);
+              part = fmaf(d, d, part);
+            }
+          }
+        } else {  // block samples, in gather_blocks' order
+          for (int w = 0; w < 8; ++w) {
+            if (gl * 8 + w < a.B0) {
+              const int c0 = (int)__umulhi(philox_word(ph, w), (uint32_t)a.Mb) * a.g;
+              const int c1 = min(c0 + a.g, m);
+              for (int c = c0; c < c1; ++c) {
+                const float d = xr[c] - __ldg(qr + c);
+                part = fmaf(d, d, part);
+              }
+            }
           }
         }
       }
@@ -946,7 +1101,24 @@ static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, Adapti
 // most kR0BufferBytes: the query chunk is sized to fit.
 constexpr size_t kR0BufferBytes = size_t(1) << 30;
 
-static inline bool round0_applies(int32_t m, const knn_opts& o) { return o.B0 < m && o.B0 <= 256; }
+static inline int32_t block_count(int32_t m, const knn_opts& o) {
+  const int32_t g = o.block > 1 ? o.block : 1;
+  return (m + g - 1) / g;
+}
+
+static inline bool round0_applies(int32_t m, const knn_opts& o) { return o.B0 < block_count(m, o) && o.B0 <= 256; }
+
+// Block samples of a launch (after a.m and a.G are set): g coordinates per
+// draw, ceil(m/g) draws to the exact distance, and whether a block is one
+// 32-byte run of the copy on 16-byte aligned rows.
+template <class E>
+static inline void set_blocks(AdaptiveArgs& a, const knn_opts& o) {
+  const size_t elem = sizeof(typename E::T);
+  const int32_t g = (E::kBlk && o.block > 1) ? o.block : 1;
+  a.g = g;
+  a.Mb = (a.m + g - 1) / g;
+  a.gvec = (g > 1 && (size_t)g * elem == 32 && ((size_t)a.m * elem) % 16 == 0 && ((uintptr_t)a.G & 15) == 0) ? 1 : 0;
+}
 
 // Queries per chunk: as many as the buffer holds, but never fewer than the
 // round-loop kernel's resident CTAs (a smaller chunk would leave SMs idle).
@@ -970,6 +1142,7 @@ static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double d
   if (o.threads != 0 && o.threads != 256 && o.threads != 512 && o.threads != 1024)
     return set_error("threads must be 0, 256, 512 or 1024"), KNN_EINVAL;
   if (o.grow != 0 && o.grow != 1) return set_error("grow must be 0 or 1"), KNN_EINVAL;
+  if (o.block < 0 || o.block > 64) return set_error("block must be in [0, 64]"), KNN_EINVAL;
   return KNN_OK;
 }
 

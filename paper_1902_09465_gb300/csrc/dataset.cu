@@ -260,6 +260,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.log_code = log_code;
   a.log_S = log_code ? log_S : nullptr;
   a.vec = (m % 4 == 0) && (((uintptr_t)ds->X & 15) == 0);
+  set_blocks<E>(a, o);
   a.R0 = r0buf;
   a.jperm = ds->jperm;
   a.mp = ds->mp;
@@ -313,7 +314,9 @@ static knn_status dispatch_ds(const knn_dataset* ds, int32_t storage, const floa
                               double delta, uint64_t seed, const knn_opts& o, int64_t* out_idx, int32_t* out_count,
                               int64_t* out_evals, int32_t* out_rounds, int32_t* log_code, float* log_S,
                               void* workspace, size_t workspace_bytes, cudaStream_t stream, const MixedBatch* mix) {
-  const bool shared = o.mask_p == 0 && o.mask_q == 0 && ((ds->share_ready >> storage) & 1) && ds->share_seed == seed;
+  // (shared-coordinate copies hold single coordinates: block samples draw per pair)
+  const bool shared = o.mask_p == 0 && o.mask_q == 0 && o.block <= 1 && ((ds->share_ready >> storage) & 1) &&
+                      ds->share_seed == seed;
 #define KNN_DS_LAUNCH(E)                                                                                        \
   return adaptive_ds_launch<E>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds, log_code, \
                                log_S, workspace, workspace_bytes, stream, mix)
@@ -321,6 +324,11 @@ static knn_status dispatch_ds(const knn_dataset* ds, int32_t storage, const floa
     if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(Perm<ElemBF16>);
     if (storage == KNN_STORE_FP8) KNN_DS_LAUNCH(Perm<ElemFP8>);
     KNN_DS_LAUNCH(Perm<ElemF32>);
+  }
+  if (o.block > 1) {
+    if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(Blk<ElemBF16>);
+    if (storage == KNN_STORE_FP8) KNN_DS_LAUNCH(Blk<ElemFP8>);
+    KNN_DS_LAUNCH(Blk<ElemF32>);
   }
   if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(ElemBF16);
   if (storage == KNN_STORE_FP8) KNN_DS_LAUNCH(ElemFP8);

@@ -35,7 +35,7 @@ class KnnError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double), ("B0", C.c_int32),
                 ("B", C.c_int32), ("grow", C.c_int32), ("qid_base", C.c_uint64), ("mask_p", C.c_uint64),
-                ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32)]
+                ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32), ("block", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -102,7 +102,10 @@ def _stream(stream):
 
 
 def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid_base=0, share_points=False,
-              share_queries=False, max_ctas=0, threads=0) -> Opts:
+              share_queries=False, max_ctas=0, threads=0, block=1) -> Opts:
+    """knn_opts for a call; `block` = coordinates per sample (1: single
+    coordinates; g > 1: blocks of g consecutive coordinates, B0 and B then
+    count blocks)."""
     o = Opts()
     lib().knn_opts_default(C.byref(o))
     o.h = -1 if h is None else int(h)
@@ -114,6 +117,7 @@ def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid
     o.mask_q = 0 if share_queries else FULL_MASK
     o.max_ctas = int(max_ctas)
     o.threads = int(threads)
+    o.block = int(block)
     return o
 
 

@@ -22,12 +22,13 @@ def run_gpu(X, Q, k, delta, seed, **opts):
 
 
 def check(X, Q, k, delta=0.01, seed=0, queries=None, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0,
-          qid_base=0, share_points=False, share_queries=False, gpu=None):
+          qid_base=0, share_points=False, share_queries=False, gpu=None, block=1, threads=0):
     """Runs the GPU (unless `gpu` holds a previous result) and replays the
     chosen queries in the oracle. Returns a summary dict."""
     if gpu is None:
         gpu = run_gpu(X, Q, k, delta, seed, h=h, bound=bound, c_alpha=c_alpha, B0=B0, B=B, grow=grow,
-                      qid_base=qid_base, share_points=share_points, share_queries=share_queries)
+                      qid_base=qid_base, share_points=share_points, share_queries=share_queries, block=block,
+                      threads=threads)
     nq, n = Q.shape[0], X.shape[0]
     hh = k if h is None else h
     kh = k + hh
@@ -36,7 +37,7 @@ def check(X, Q, k, delta=0.01, seed=0, queries=None, h=None, bound="footnote", c
     for q in queries:
         p = oracle.make_params(k, h=hh, delta=delta, bound=bound, c_alpha=c_alpha, B0=B0, B=B, grow=grow, seed=seed,
                                qid=qid_base + q, share_points=share_points, share_queries=share_queries,
-                               tol=TOL_DECISION)
+                               tol=TOL_DECISION, block=block)
         o = oracle.adaptive(X, Q[q:q + 1], p, replay=gpu["code"][q:q + 1])
         st = o["stats"][0]
         assert st["mismatch"] == 0, (q, st)
@@ -61,7 +62,7 @@ def check(X, Q, k, delta=0.01, seed=0, queries=None, h=None, bound="footnote", c
             assert g_set == o_set == set(live.tolist())
         elif g_set != o_set:
             # truncation by estimate: any difference must be a near-tie
-            dh = So / np.maximum(o["T"][0], 1)
+            dh = So / (np.maximum(o["T"][0], 1) * max(block, 1))
             bound_v = max(dh[list(o_set)])
             for i in g_set ^ o_set:
                 assert abs(dh[i] - bound_v) <= 1e-5 * max(abs(bound_v), 1e-300), (q, i)
