@@ -547,6 +547,97 @@ def run_serve(args):
         ds.close()
 
 
+SWEEP = dict(name="precision sweep: planted neighbours over N(0,1), n=200000 d=1024 nq=4096 k=10 delta=0.01",
+             n=200_000, m=1024, nq=4096, k=10, delta=0.01, gaps=(1.05, 1.2, 1.5, 2.0, 4.0), nheld=256)
+
+
+def run_sweep(args):
+    """Precision sweep: for each gap ratio, one dataset (n = 200,000, d =
+    1,024, N(0,1) background, 10 planted neighbours per query at distance
+    D_far / gap); the exact method against the adaptive variants (per-pair
+    draws over FP32 / BF16 / FP8 copies, 32-byte block samples, shared
+    coordinates), each autotuned on 256 held-out queries to recall >= 0.999
+    and timed over 4,096 queries (rounds + FP64 rerank, CUDA graph)."""
+    import torch
+    from paper_1902_09465_gb300 import knn, runtime, synth
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = SWEEP
+    n, m, nq, k, delta = w["n"], w["m"], w["nq"], w["k"], w["delta"]
+    gaps = [float(g) for g in args.sweep_gaps.split(",")] if args.sweep_gaps else list(w["gaps"])
+    cgrid = [1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6]
+    variants = [  # name, storage, extra options, schedules
+        ("per_pair_f32", "f32", {}, ((8, 8, 1), (16, 16, 1))),
+        ("per_pair_bf16", "bf16", {}, ((8, 8, 1), (16, 16, 1))),
+        ("per_pair_fp8", "fp8", {}, ((8, 8, 1), (16, 16, 1))),
+        ("blocks_f32_g8", "f32", {"block": 8}, ((2, 2, 1), (4, 4, 1), (8, 8, 1))),
+        ("blocks_bf16_g16", "bf16", {"block": 16}, ((2, 2, 1), (4, 4, 1), (8, 8, 1))),
+        ("blocks_fp8_g32", "fp8", {"block": 32}, ((2, 2, 1), (4, 4, 1))),
+        ("shared_f32", "f32", {"share_points": True, "share_queries": True}, ((16, 16, 1), (32, 32, 1))),
+        ("shared_bf16", "bf16", {"share_points": True, "share_queries": True}, ((16, 16, 1), (32, 32, 1))),
+    ]
+    if args.sweep_variants:
+        keep = set(args.sweep_variants.split(","))
+        variants = [v for v in variants if v[0] in keep]
+    results = []
+    for gi, gap in enumerate(gaps):
+        X, Qall, _ = synth.gap_planted(n, m, nq + w["nheld"], k, gap, seed=500 + gi)
+        Xd = torch.from_numpy(X).to(dev)
+        Qd = torch.from_numpy(Qall[:nq]).to(dev)
+        Hd = torch.from_numpy(Qall[nq:]).to(dev)
+        ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen"))
+        ds.share(0, copies=("f32", "bf16"))
+        ti, td = ds.exact(Qd, k, screen="f32")
+        tin, tdn = ti.cpu().numpy(), td.cpu().numpy()
+
+        def timed(fn, steps=3):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps, out
+
+        row = {"gap": gap}
+        ex_ms, (ei, _) = timed(lambda: ds.exact(Qd, k, screen="bf16x3"))
+        row["exact_tc"] = {"queries_per_s": round(nq / (ex_ms / 1e3), 1), "ms": round(ex_ms, 3),
+                           "agrees": bool(torch.equal(ei, ti))}
+        sm_ms, _ = timed(lambda: ds.exact(Qd, k, screen="f32"), steps=1)
+        row["exact_simt"] = {"queries_per_s": round(nq / (sm_ms / 1e3), 1), "ms": round(sm_ms, 3)}
+        for name, storage, extra, scheds in variants:
+            try:
+                t = runtime.autotune(ds, Hd, k, delta, storage=storage, target=RECALL_TARGET, margin=0.0005,
+                                     schedules=scheds, threads=(512, 1024), c_grid=cgrid, use_cache=False,
+                                     extra=extra, reps=2,
+                                     cache=os.path.join(tempfile.gettempdir(), f"knn_sweep_{os.getpid()}.json"))
+            except knn.KnnError as e:
+                row[name] = {"error": str(e)}
+                continue
+            b = t["best"]
+            opts = dict(bound="exp", c_alpha=b["c_alpha"], B0=b["B0"], B=b["B"], grow=b["grow"], threads=b["threads"],
+                        **extra)
+            step = runtime.GraphStep(ds, nq, k, delta, 0, storage=storage, **opts)
+            ms, (res, ri, rd) = timed(lambda: step.run(Qd))
+            ev = int(res["evals"].sum().item())
+            row[name] = {"queries_per_s": round(nq / (ms / 1e3), 1), "ms": round(ms, 3),
+                         "recall": round(recall_of(ri.cpu().numpy(), rd.cpu().numpy(), tin, tdn), 6),
+                         "coord_evals_fraction": round(ev / (nq * n * m), 6), "tuned": b}
+            del step
+        print(json.dumps(row), flush=True)
+        results.append(row)
+        ds.close()
+        del Xd, Qd, Hd
+        torch.cuda.empty_cache()
+    out = {"metric": "k-NN queries/s at recall>=0.999 per gap ratio (adaptive variants vs exact)",
+           "unit": "queries/s", "n_gpus": 1, "data": "synthetic", "config": {"workload": w["name"]},
+           "gaps": results}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -561,6 +652,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nq", type=int, default=None, help="queries per GPU (default 1024)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
+    ap.add_argument("--sweep", action="store_true", help="run the gap-ratio precision sweep instead")
+    ap.add_argument("--sweep-gaps", dest="sweep_gaps", default=None, help="comma-separated gap ratios")
+    ap.add_argument("--sweep-variants", dest="sweep_variants", default=None, help="comma-separated variant names")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=5.0)
     ap.add_argument("--serve-scale", dest="serve_scale", type=float, default=1.0)
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
@@ -580,6 +674,10 @@ def main():
     if args.serve:
         if rank == 0:
             run_serve(args)
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args)
         return
 
     if args.impl == "reference":

@@ -33,8 +33,11 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
   if (ps != KNN_OK) return 0;
   Carve cv;
   carve_adaptive(cv, n, p, nullptr);
-  if (round0_applies(m, o) || (o.block <= 1 && o.B0 < m && o.B0 <= 16))  // dataset paths only
-    cv.take<float>((size_t)round0_chunk(n, nq, p.grid) * (size_t)n);
+  if (round0_applies(m, o) || (o.block <= 1 && o.B0 < m && o.B0 <= 16)) {  // dataset paths only
+    const size_t chunk = (size_t)round0_chunk(n, nq, p.grid);
+    cv.take<float>(chunk * (size_t)n);                                      // round-0 sums
+    cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // their tile minima
+  }
   return cv.off + 256;
 }
 
@@ -103,6 +106,8 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.h_per_k = 0;
   a.out_stride = k + o.h;
   a.R0 = nullptr;
+  a.R0min = nullptr;
+  a.r0tiles = 0;
   a.jperm = nullptr;
   a.mp = 0;
   a.bound = o.bound;
@@ -259,6 +264,8 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.h_per_k = 0;
   a.out_stride = k + o.h;
   a.R0 = nullptr;
+  a.R0min = nullptr;
+  a.r0tiles = 0;
   a.jperm = nullptr;
   a.mp = 0;
   a.bound = o.bound;

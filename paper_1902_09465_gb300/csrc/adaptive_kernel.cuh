@@ -74,6 +74,8 @@ struct AdaptiveArgs {
   int32_t Mb;   // samples that make a distance exact: ceil(m / g)
   int32_t gvec; // a block is 32 bytes of the copy on 16-byte aligned rows: two 16-byte loads
   const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
+  const float* R0min;   // smallest round-0 sum of each tile of points [nq][r0tiles] (null: no filter)
+  int32_t r0tiles;      // tiles per query in R0min
   const int32_t* jperm; // shared-coordinate copies: column of draw t (t < m), for Perm element types
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
 };
@@ -529,6 +531,83 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
   }
 }
 
+// Round 0 from the point-major pass, with tile minima. tau_U' = (k-th
+// smallest tile minimum)/T + w is at least tau_U (the k smallest tile minima
+// are sums of k distinct points), so a point whose LCB exceeds tau_U' is
+// eliminated whatever the other sums are. One streaming pass drops those
+// points (logged; their smallest LCB joins min_elim) and keeps the others in
+// index order (idA/SA); the round then runs on the kept points alone. The k
+// smallest sums are always kept, so tau_U is unchanged, and the (k+1)-th
+// smallest LCB over all points is the smaller of the kept points' (k+1)-th
+// and the dropped points' smallest. hist holds zeros on entry and the level-1
+// counts of the kept keys on exit; stI/stS are staging space of n entries.
+template <int NT>
+__device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, float w, float Tf, uint32_t* hist,
+                             uint32_t* buf, AdaptiveShared<NT>& sh, int32_t* idA, float* SA, int32_t* stI,
+                             float* stS, int32_t* lcode, float* lS, float* min_elim) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* mq = a.R0min + (size_t)q * (size_t)a.r0tiles;
+  const int nt = a.r0tiles;
+  for (int i = tid; i < nt; i += NT) atomicAdd(&hist[f2key(mq[i]) >> 20], 1u);
+  __syncthreads();
+  select_smallest<NT>([&](int i) { return f2key(mq[i]); }, nt, k, hist, buf, sh.ss, sh.bs);
+  const float tU = key2f(buf[k - 1]) / Tf + w;  // the UCB of that sum, formed as the thresholds form it
+  for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
+  __syncthreads();
+  // warp w scans its own contiguous segment, U loads in flight per lane;
+  // ballots keep the order inside the warp, the warps' counts the order across
+  constexpr int U = 8;
+  constexpr int NW = NT / 32;
+  const int64_t seg = ((n + NW - 1) / NW + 31) & ~(int64_t)31;
+  const int64_t s0 = (int64_t)warp * seg, s1 = min(n, s0 + seg);
+  const float* R0q = a.R0 + (size_t)q * (size_t)n;
+  int cnt = 0;
+  float mn = INFINITY;
+  for (int64_t base = s0; base < s1; base += 32 * U) {
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * 32 + lane;
+      v[u] = i < s1 ? __ldcs(R0q + i) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * 32 + lane;
+      bool keep = false;
+      if (i < s1) {
+        const float L = v[u] / Tf - w;  // the LCB as the decide pass forms it
+        if (L > tU) {
+          mn = fminf(mn, L);
+          if (lcode) {
+            lcode[i] = 1;  // eliminated in round 0
+            if (lS) lS[i] = v[u];
+          }
+        } else {
+          keep = true;
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        stI[s0 + pos] = (int32_t)i;
+        stS[s0 + pos] = v[u];
+        atomicAdd(&hist[f2key(v[u]) >> 20], 1u);
+      }
+      cnt += __popc(bal);
+    }
+  }
+  int total;
+  const int off = block_exclusive_scan<NT>(lane == 0 ? cnt : 0, sh.bs, &total);  // barriers order the staging
+  const int woff = __shfl_sync(0xffffffffu, off, 0);
+  for (int t = lane; t < cnt; t += 32) {
+    idA[woff + t] = stI[s0 + t];
+    SA[woff + t] = stS[s0 + t];
+  }
+  mn = block_min<NT>(mn, sh.bs);
+  *min_elim = fminf(*min_elim, mn);
+  return total;
+}
+
 template <int NT, class E>
 __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(AdaptiveArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -639,11 +718,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       const int64_t Tn = exact ? a.Mb : T + Br;
       const int32_t* idc = ids0 + (size_t)cur * n;
       const bool pre = (r == 0) && a.R0 && !exact;  // round-0 sums computed point-major beforehand
-      float* Sc = pre ? const_cast<float*>(a.R0) + (size_t)q * (size_t)n : S0 + (size_t)cur * n;
+      // with tile minima, round 0 first drops the points they already prove eliminated
+      const bool flt = pre && a.R0min && a.r0tiles >= k;
+      float* Sc = pre && !flt ? const_cast<float*>(a.R0) + (size_t)q * (size_t)n : S0 + (size_t)cur * n;
       float* Cc = C0 + (size_t)cur * n;
+      evals += (int64_t)nact * (exact ? (int64_t)m : Br * a.g);
+      const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
+      const float Tf = (float)(Tn * a.g);  // estimate = S / (T g): mean per coordinate
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
-      if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
+      if (flt)
+        nact = round0_filter<NT>(a, q, n, k, w, Tf, hist, buf, sh, ids0 + (size_t)cur * n, Sc,
+                                 ids0 + (size_t)(cur ^ 1) * n, S0 + (size_t)(cur ^ 1) * n, lcode, lS, &min_elim);
+      else if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
       else if (pre)
         for (int i = tid; i < nact; i += NT) atomicAdd(&hist[f2key(Sc[i]) >> 20], 1u);
@@ -652,9 +739,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       else
         gather_sampled<NT, E>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
-      evals += (int64_t)nact * (exact ? (int64_t)m : Br * a.g);
-      const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
-      const float Tf = (float)(Tn * a.g);  // estimate = S / (T g): mean per coordinate
+      const bool ident = (r == 0) && !flt;  // slot s holds point s
 
       // ---- thresholds
       const int kk = min(k + 1, nact);
@@ -667,7 +752,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       if (tid == 0) sh.nacc_add = 0;
       __syncthreads();
       const float tauU = kth_of_union<NT>(actU, min(k, nact), acc_U, nacc, k, &sh.tauU);
-      const float tauL = fminf(kth_of_union<NT>(actL, kk, acc_L, nacc, k + 1, &sh.tauL), min_elim);
+      // (after the round-0 filter the kept points can number k: the (k+1)-th
+      // smallest LCB is then that of a dropped point, min_elim)
+      const float tauL = nact + nacc > k ? fminf(kth_of_union<NT>(actL, kk, acc_L, nacc, k + 1, &sh.tauL), min_elim)
+                                         : min_elim;
 
       // ---- decide + compact (order-preserving)
       int32_t* idn = ids0 + (size_t)(cur ^ 1) * n;
@@ -688,7 +776,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
           myS[e] = 0.0f;
           myC[e] = 0.0f;
           if (s < nact) {
-            const int id = (r == 0) ? s : idc[s];
+            const int id = ident ? s : idc[s];
             const float S = Sc[s];
             const float c = (r == 0 || exact) ? 0.0f : Cc[s];
             const float d = S / Tf;
@@ -855,7 +943,8 @@ static inline int round0_rows(int m) {
 }
 
 template <class E>
-__global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int rows_per_cta, float* R0) {
+__global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int rows_per_cta, float* R0,
+                                                            float* R0min) {
   extern __shared__ __align__(16) float rows[];
   using Tp = typename E::T;
   const int m = a.m;
@@ -880,6 +969,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
     const uint64_t qid = a.qids ? a.qids[q] : a.qid_base + (uint64_t)q;
     const uint64_t qfield = qid & a.mask_q;
     const float* qr = a.Q + (size_t)q * m;
+    float tmin = INFINITY;  // smallest sum of this CTA's rows for query q
     for (int base = 0; base < np; base += ppw) {
       const int pi = base + grp;
       float part = 0.0f;
@@ -912,7 +1002,15 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
 #pragma unroll
       for (int o = 16; o; o >>= 1)
         if (o < G) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (pi < np && gl == 0) R0[(size_t)q * (size_t)n + p0 + pi] = part;
+      if (pi < np && gl == 0) {
+        R0[(size_t)q * (size_t)n + p0 + pi] = part;
+        tmin = fminf(tmin, part);
+      }
+    }
+    if (R0min) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+      if (lane == 0) R0min[(size_t)q * gridDim.x + blockIdx.x] = tmin;
     }
   }
 }
@@ -927,7 +1025,7 @@ constexpr int kR0SharedThreads = 256;
 constexpr int kR0SharedQueries = 256;  // queries staged at a time
 
 template <class E>
-__global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, float* R0) {
+__global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, float* R0, float* R0min) {
   __shared__ float qv[kR0SharedQueries * 16];
   using Tp = typename E::T;
   const int m = a.m;
@@ -935,6 +1033,8 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
   const int B0 = a.B0;
   const int64_t i = (int64_t)blockIdx.x * kR0SharedThreads + threadIdx.x;
   float x[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) x[t] = 0.0f;
   if (i < n) {
     const Tp* xr = static_cast<const Tp*>(a.G) + (size_t)i * (size_t)a.mp;
     const float sc = E::kScaled ? __ldg(a.gscale + i) : 1.0f;
@@ -951,7 +1051,7 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
       qv[e] = t < B0 ? __ldg(a.Q + (size_t)(q0 + qq) * m + a.jperm[t]) : 0.0f;
     }
     __syncthreads();
-    if (i < n) {
+    if (((int64_t)blockIdx.x * kR0SharedThreads + (threadIdx.x & ~31)) < n) {  // warp-uniform
       for (int qq = 0; qq < qc; ++qq) {
         const float* v = qv + qq * 16;
         float p0 = 0.0f, p1 = 0.0f;
@@ -967,7 +1067,14 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
             const float d = x[w] - v[w];
             p1 = fmaf(d, d, p1);
           }
-        R0[(size_t)(q0 + qq) * (size_t)n + i] = B0 > 8 ? p0 + p1 : p0;
+        const float S = B0 > 8 ? p0 + p1 : p0;
+        if (i < n) R0[(size_t)(q0 + qq) * (size_t)n + i] = S;
+        if (R0min) {  // smallest sum of the warp's 32 points
+          float t = i < n ? S : INFINITY;
+#pragma unroll
+          for (int o = 16; o; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
+          if ((threadIdx.x & 31) == 0) R0min[(size_t)(q0 + qq) * (size_t)a.r0tiles + (size_t)(i >> 5)] = t;
+        }
       }
     }
   }

@@ -193,9 +193,15 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   knn_status s = plan_adaptive<E>(n, m, nq, k, &o, &p);
   if (s != KNN_OK) return s;
   const int chunk = r0 ? round0_chunk(n, nq, p.grid) : nq;
+  // round-0 tile minima: per CTA of the staged-rows pass, per warp of the shared pass
+  const int rows = round0_rows(m);
+  const int tiles = !r0 ? 0 : (int)(E::kPerm ? (n + 31) / 32 : (n + rows - 1) / rows);
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
-  if (r0) measure.take<float>((size_t)chunk * (size_t)n);
+  if (r0) {
+    measure.take<float>((size_t)chunk * (size_t)n);
+    measure.take<float>((size_t)chunk * (size_t)tiles);
+  }
   const size_t need = measure.off + 256;
   Workspace ws;
   s = ws.acquire(workspace, workspace_bytes, need, stream);
@@ -205,6 +211,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   AdaptiveCarve c;
   carve_adaptive(cv, n, p, &c);
   float* r0buf = r0 ? cv.take<float>((size_t)chunk * (size_t)n) : nullptr;
+  float* r0min = r0 ? cv.take<float>((size_t)chunk * (size_t)tiles) : nullptr;
   AdaptiveArgs a;
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
@@ -262,9 +269,10 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   a.vec = (m % 4 == 0) && (((uintptr_t)ds->X & 15) == 0);
   set_blocks<E>(a, o);
   a.R0 = r0buf;
+  a.R0min = r0min;
+  a.r0tiles = tiles;
   a.jperm = ds->jperm;
   a.mp = ds->mp;
-  const int rows = round0_rows(m);
   if (r0 && !E::kPerm) {
     s = cuda_check(cudaFuncSetAttribute(round0_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)((size_t)rows * m * 4)),
@@ -293,11 +301,11 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
     if (s == KNN_OK && r0) {
       if constexpr (E::kPerm) {
         const unsigned blocks = (unsigned)((n + kR0SharedThreads - 1) / kR0SharedThreads);
-        round0_shared_kernel<E><<<blocks, kR0SharedThreads, 0, stream>>>(ac, r0buf);
+        round0_shared_kernel<E><<<blocks, kR0SharedThreads, 0, stream>>>(ac, r0buf, r0min);
         s = cuda_check(cudaGetLastError(), "round0_shared_kernel launch");
       } else {
         const unsigned blocks = (unsigned)((n + rows - 1) / rows);
-        round0_kernel<E><<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf);
+        round0_kernel<E><<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf, r0min);
         s = cuda_check(cudaGetLastError(), "round0_kernel launch");
       }
     }
