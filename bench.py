@@ -566,7 +566,7 @@ def run_sweep(args):
     w = SWEEP
     n, m, nq, k, delta = w["n"], w["m"], w["nq"], w["k"], w["delta"]
     gaps = [float(g) for g in args.sweep_gaps.split(",")] if args.sweep_gaps else list(w["gaps"])
-    cgrid = [1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6]
+    cgrid = [1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5, 3e-6, 1e-6, 3e-7]
     variants = [  # name, storage, extra options, schedules
         ("per_pair_f32", "f32", {}, ((8, 8, 1), (16, 16, 1))),
         ("per_pair_bf16", "bf16", {}, ((8, 8, 1), (16, 16, 1))),
@@ -574,8 +574,10 @@ def run_sweep(args):
         ("blocks_f32_g8", "f32", {"block": 8}, ((2, 2, 1), (4, 4, 1), (8, 8, 1))),
         ("blocks_bf16_g16", "bf16", {"block": 16}, ((2, 2, 1), (4, 4, 1), (8, 8, 1))),
         ("blocks_fp8_g32", "fp8", {"block": 32}, ((2, 2, 1), (4, 4, 1))),
-        ("shared_f32", "f32", {"share_points": True, "share_queries": True}, ((16, 16, 1), (32, 32, 1))),
-        ("shared_bf16", "bf16", {"share_points": True, "share_queries": True}, ((16, 16, 1), (32, 32, 1))),
+        ("shared_f32", "f32", {"share_points": True, "share_queries": True},
+         ((8, 8, 1), (16, 16, 1), (32, 32, 1), (64, 64, 1))),
+        ("shared_bf16", "bf16", {"share_points": True, "share_queries": True},
+         ((8, 8, 1), (16, 16, 1), (32, 32, 1), (64, 64, 1))),
     ]
     if args.sweep_variants:
         keep = set(args.sweep_variants.split(","))

@@ -33,10 +33,11 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
   if (ps != KNN_OK) return 0;
   Carve cv;
   carve_adaptive(cv, n, p, nullptr);
-  if (round0_applies(m, o) || (o.block <= 1 && o.B0 < m && o.B0 <= 16)) {  // dataset paths only
+  if (round0_applies(m, o) || (o.block <= 1 && o.B0 < m && o.B0 <= 64)) {  // dataset paths only
     const size_t chunk = (size_t)round0_chunk(n, nq, p.grid);
     cv.take<float>(chunk * (size_t)n);                                      // round-0 sums
     cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // their tile minima
+    cv.take<float>(chunk * 64);                                             // permuted query columns
   }
   return cv.off + 256;
 }

@@ -1019,63 +1019,103 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
 // B0 columns of its permuted row, so one thread per point reads them once and
 // forms the round-0 sum with every query of the chunk (their permuted values
 // staged in shared memory). The sum follows the round-loop kernel's order:
-// each block of 8 draws in sequence, then the two blocks added (the lane
-// butterfly for G = 2). Needs B0 <= 16.
+// each block of 8 draws in sequence into its own partial, then the partials
+// combined as the lane butterfly of the round loop combines them (G lanes,
+// G the power of two at or above the number of blocks). NB blocks of 8 at
+// most: B0 <= 8 NB.
 constexpr int kR0SharedThreads = 256;
-constexpr int kR0SharedQueries = 256;  // queries staged at a time
 
-template <class E>
-__global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, float* R0, float* R0min) {
-  __shared__ float qv[kR0SharedQueries * 16];
+template <int NB>
+struct R0SharedCfg {
+  static constexpr int kQueries = NB <= 2 ? 256 : 64;  // queries staged at a time (16 KB)
+};
+
+// The chunk's query values at the first W permuted columns (zero past B0),
+// row-major [nq][W], so the round-0 pass stages them with plain loads.
+static __global__ void permute_query_columns_kernel(const float* __restrict__ Q, int m, int nq,
+                                                    const int32_t* __restrict__ jperm, int B0, int W,
+                                                    float* __restrict__ Qp) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)nq * W) return;
+  const int q = (int)(e / W), t = (int)(e - (int64_t)q * W);
+  Qp[e] = t < B0 ? __ldg(Q + (size_t)q * m + jperm[t]) : 0.0f;
+}
+
+template <class E, int NB>
+__global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, const float* Qp, float* R0,
+                                                                         float* R0min) {
+  // grid: x = tiles of kR0SharedThreads points, y = slices of kQ queries
+  constexpr int W = 8 * NB;
+  constexpr int kQ = R0SharedCfg<NB>::kQueries;
+  __shared__ __align__(16) float qv[kQ * W];
   using Tp = typename E::T;
-  const int m = a.m;
   const int64_t n = a.n;
   const int B0 = a.B0;
+  const int nfull = B0 >> 3, rem = B0 & 7;
+  const int nblk = nfull + (rem ? 1 : 0);
+  int G = 1;
+  while (G < nblk) G <<= 1;
   const int64_t i = (int64_t)blockIdx.x * kR0SharedThreads + threadIdx.x;
-  float x[16];
+  const int q0 = (int)blockIdx.y * kQ;
+  const int qc = min(kQ, a.nq - q0);
+  {
+    const float4* src = reinterpret_cast<const float4*>(Qp + (size_t)q0 * W);
+    float4* dst = reinterpret_cast<float4*>(qv);
+    for (int e = threadIdx.x; e < qc * W / 4; e += kR0SharedThreads) dst[e] = __ldg(src + e);
+  }
+  float x[W];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) x[t] = 0.0f;
+  for (int t = 0; t < W; ++t) x[t] = 0.0f;
   if (i < n) {
     const Tp* xr = static_cast<const Tp*>(a.G) + (size_t)i * (size_t)a.mp;
     const float sc = E::kScaled ? __ldg(a.gscale + i) : 1.0f;
-    load8<E>(xr, x);
-    if (B0 > 8) load8<E>(xr + 8, x + 8);
 #pragma unroll
-    for (int t = 0; t < 16; ++t) x[t] = E::kScaled ? __fmul_rn(x[t], sc) : x[t];
+    for (int b = 0; b < NB; ++b)
+      if (b < nblk) load8<E>(xr + 8 * b, x + 8 * b);
+#pragma unroll
+    for (int t = 0; t < W; ++t) x[t] = E::kScaled ? __fmul_rn(x[t], sc) : x[t];
   }
-  for (int q0 = 0; q0 < a.nq; q0 += kR0SharedQueries) {
-    const int qc = min(kR0SharedQueries, a.nq - q0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < qc * 16; e += kR0SharedThreads) {
-      const int qq = e >> 4, t = e & 15;
-      qv[e] = t < B0 ? __ldg(a.Q + (size_t)(q0 + qq) * m + a.jperm[t]) : 0.0f;
-    }
-    __syncthreads();
-    if (((int64_t)blockIdx.x * kR0SharedThreads + (threadIdx.x & ~31)) < n) {  // warp-uniform
-      for (int qq = 0; qq < qc; ++qq) {
-        const float* v = qv + qq * 16;
-        float p0 = 0.0f, p1 = 0.0f;
+  __syncthreads();
+  if (((int64_t)blockIdx.x * kR0SharedThreads + (threadIdx.x & ~31)) >= n) return;  // warp-uniform
+  for (int qq = 0; qq < qc; ++qq) {
+    const float4* v4 = reinterpret_cast<const float4*>(qv + qq * W);
+    float p[NB];
 #pragma unroll
-        for (int w = 0; w < 8; ++w)
-          if (w < B0) {
-            const float d = x[w] - v[w];
-            p0 = fmaf(d, d, p0);
+    for (int b = 0; b < NB; ++b) {
+      p[b] = 0.0f;
+      if (b < nfull || (b == nfull && rem)) {  // uniform over the grid
+        const float4 va = v4[2 * b], vb = v4[2 * b + 1];
+        const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        if (b < nfull) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            const float d = x[8 * b + w] - vv[w];
+            p[b] = fmaf(d, d, p[b]);
           }
+        } else {
 #pragma unroll
-        for (int w = 8; w < 16; ++w)
-          if (w < B0) {
-            const float d = x[w] - v[w];
-            p1 = fmaf(d, d, p1);
-          }
-        const float S = B0 > 8 ? p0 + p1 : p0;
-        if (i < n) R0[(size_t)(q0 + qq) * (size_t)n + i] = S;
-        if (R0min) {  // smallest sum of the warp's 32 points
-          float t = i < n ? S : INFINITY;
-#pragma unroll
-          for (int o = 16; o; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
-          if ((threadIdx.x & 31) == 0) R0min[(size_t)(q0 + qq) * (size_t)a.r0tiles + (size_t)(i >> 5)] = t;
+          for (int w = 0; w < 8; ++w)
+            if (w < rem) {
+              const float d = x[8 * b + w] - vv[w];
+              p[b] = fmaf(d, d, p[b]);
+            }
         }
       }
+    }
+#pragma unroll
+    for (int o = NB / 2; o; o >>= 1)
+      if (o < G) {
+#pragma unroll
+        for (int j = 0; j < o; ++j) p[j] += p[j + o];
+      }
+    const float S = p[0];
+    const int qg = q0 + qq;
+    if (i < n) R0[(size_t)qg * (size_t)n + i] = S;
+    if (R0min) {  // smallest sum of the warp's 32 points
+      float t = i < n ? S : INFINITY;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
+      if ((threadIdx.x & 31) == 0) R0min[(size_t)qg * (size_t)a.r0tiles + (size_t)(i >> 5)] = t;
     }
   }
 }

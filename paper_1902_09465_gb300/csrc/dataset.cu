@@ -187,8 +187,8 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
                                      const MixedBatch* mix = nullptr) {
   const int64_t n = ds->n;
   const int32_t m = ds->m;
-  // round 0 point-major: the shared form for B0 <= 16, the staged-rows pass otherwise
-  const bool r0 = E::kPerm ? (o.B0 < m && o.B0 <= 16) : round0_applies(m, o);
+  // round 0 point-major: the shared form for B0 <= 64, the staged-rows pass otherwise
+  const bool r0 = E::kPerm ? (o.B0 < m && o.B0 <= 64) : round0_applies(m, o);
   AdaptivePlan p;
   knn_status s = plan_adaptive<E>(n, m, nq, k, &o, &p);
   if (s != KNN_OK) return s;
@@ -198,9 +198,11 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   const int tiles = !r0 ? 0 : (int)(E::kPerm ? (n + 31) / 32 : (n + rows - 1) / rows);
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
+  const int qpw = E::kPerm && r0 ? (o.B0 <= 16 ? 16 : 64) : 0;  // permuted query columns staged by round 0
   if (r0) {
     measure.take<float>((size_t)chunk * (size_t)n);
     measure.take<float>((size_t)chunk * (size_t)tiles);
+    measure.take<float>((size_t)chunk * (size_t)qpw);
   }
   const size_t need = measure.off + 256;
   Workspace ws;
@@ -212,6 +214,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   carve_adaptive(cv, n, p, &c);
   float* r0buf = r0 ? cv.take<float>((size_t)chunk * (size_t)n) : nullptr;
   float* r0min = r0 ? cv.take<float>((size_t)chunk * (size_t)tiles) : nullptr;
+  float* qperm = qpw ? cv.take<float>((size_t)chunk * (size_t)qpw) : nullptr;
   AdaptiveArgs a;
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
@@ -301,7 +304,18 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
     if (s == KNN_OK && r0) {
       if constexpr (E::kPerm) {
         const unsigned blocks = (unsigned)((n + kR0SharedThreads - 1) / kR0SharedThreads);
-        round0_shared_kernel<E><<<blocks, kR0SharedThreads, 0, stream>>>(ac, r0buf, r0min);
+        const int64_t cnt = (int64_t)ac.nq * qpw;
+        permute_query_columns_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(ac.Q, m, ac.nq, ds->jperm,
+                                                                                         o.B0, qpw, qperm);
+        s = cuda_check(cudaGetLastError(), "permute_query_columns_kernel launch");
+        if (s != KNN_OK) break;
+        if (o.B0 <= 16) {
+          const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<2>::kQueries - 1) / R0SharedCfg<2>::kQueries));
+          round0_shared_kernel<E, 2><<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
+        } else {
+          const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<8>::kQueries - 1) / R0SharedCfg<8>::kQueries));
+          round0_shared_kernel<E, 8><<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
+        }
         s = cuda_check(cudaGetLastError(), "round0_shared_kernel launch");
       } else {
         const unsigned blocks = (unsigned)((n + rows - 1) / rows);

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 SH = dict(share_points=True, share_queries=True)
 
 
-@pytest.mark.parametrize("m,B0", [(784, 8), (784, 16), (77, 12), (5, 3), (300, 32)])
+@pytest.mark.parametrize("m,B0", [(784, 8), (784, 16), (77, 12), (5, 3), (300, 32), (784, 64), (200, 40), (100, 24)])
 def test_shared_copies_equal_per_pair_draws(m, B0):
     X, Q = synth.pixel_mixture(12000, m, 24, seed=m)
     Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
