@@ -356,6 +356,36 @@ def run_ours(args, rank, world, local_rank):
             "tuned": b, "coord_evals_fraction": round(ev_s / (nq * n * m), 6),
             "alg_gbs_step": round(elem * ev_s / (ms_s / 1e3) / 1e9, 2)}
 
+    # ---- block samples (a draw reads one 32-byte block: 8 FP32 / 16 BF16 coordinates)
+    blocks = {}
+    for storage, g in (("f32", 8), ("bf16", 16)):
+        t = runtime.autotune(ds, Hd, k, w["delta"], storage=storage, target=RECALL_TARGET, margin=0.0005,
+                             schedules=((2, 2, 1), (4, 4, 1), (8, 8, 1)), use_cache=False, extra={"block": g},
+                             c_grid=[args.c_alpha] if args.c_alpha else C_GRID + [1e-5, 3e-6],
+                             cache=os.path.join(tempfile.gettempdir(), f"knn_bench_tune_blk_{os.getpid()}.json"))
+        b = t["best"]
+        o_b = dict(opts_of(b), block=g)
+        step = runtime.GraphStep(ds, nq, k, w["delta"], 0, storage=storage, qid_base=qid_base, **o_b)
+        for _ in range(2):
+            step.run(Qd)
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        vsteps = max(2, min(args.steps, 5))
+        for _ in range(vsteps):
+            res_s, ri_s, rd_s = step.run(Qd)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = max_over_ranks(v0.elapsed_time(v1) / vsteps)
+        ev_s = int(res_s["evals"].sum().item())
+        elem = 4 if storage == "f32" else 2
+        blocks[f"{storage}_g{g}"] = {
+            "queries_per_s": round(world * nq / (ms_s / 1e3), 3), "ms_per_step": round(ms_s, 4),
+            "recall": round(recall_of(ri_s.cpu().numpy(), rd_s.cpu().numpy(), ti_np, td_np), 6),
+            "tuned": b, "coord_evals_fraction": round(ev_s / (nq * n * m), 6),
+            "alg_gbs_step": round(elem * ev_s / (ms_s / 1e3) / 1e9, 2)}
+
     # ---- end to end through the public API with host buffers
     Qh = torch.from_numpy(Q).pin_memory()
     ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
@@ -401,6 +431,7 @@ def run_ours(args, rank, world, local_rank):
         "rounds_mean": round(float(rounds.mean()), 3),
         "storage_variants": variants,
         "shared_coordinates": shared,
+        "block_samples": blocks,
         "exact_baseline": {"queries_per_s": round(world * nq / (exact_ms / 1e3), 3), "ms_per_batch": round(exact_ms, 4),
                            "method": "tcgen05 BF16x3 screen GEMM + select + FP64 rerank (exact)",
                            "agrees_with_simt_path": exact_agree,
@@ -640,6 +671,55 @@ def run_sweep(args):
     print(json.dumps(out), flush=True)
 
 
+FIG2 = dict(n=1000, m=12288, k=10, h=10, delta=0.001, trials=20, ps=(10, 100, 1000),
+            c_grid=(1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, 3e-1, 1.0))
+
+
+def run_figure2(args):
+    """Section 5's experiment (Figure 2) on the GPU path: n = 1,000 points in
+    m = 12,288 dimensions, k = h = 10, delta = 0.001, the Section 5 bound with
+    C_alpha swept; per C_alpha, 20 trials (a fresh dataset and query each),
+    the median and interquartile range of the recall (fraction of the true k
+    nearest inside the returned set) and of the evaluation ratio against the
+    naive method (coordinate evaluations / (n m)). Data: the subspace model
+    x = c Q y for p in {10, 100, 1000}, and the pixel mixture standing in for
+    Tiny ImageNet images (not available here)."""
+    import torch
+    from paper_1902_09465_gb300 import knn, synth
+
+    torch.cuda.set_device(0)
+    f = FIG2
+    n, m, k, h, delta = f["n"], f["m"], f["k"], f["h"], f["delta"]
+    datasets = [(f"subspace p={p}", lambda t, p=p: synth.subspace(n, m, p, nq=1, seed=7000 + 31 * p + t))
+                for p in f["ps"]]
+    datasets.append(("pixel mixture (Tiny ImageNet stand-in)",
+                     lambda t: synth.pixel_mixture(n, m, 1, n_centres=100, sigma=0.1, seed=9000 + t)))
+    series = []
+    for name, gen in datasets:
+        rec = np.zeros((f["trials"], len(f["c_grid"])))
+        ratio = np.zeros_like(rec)
+        for t in range(f["trials"]):
+            X, Q = gen(t)
+            Xd, Qd = torch.from_numpy(np.ascontiguousarray(X)).cuda(), torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+            ti, _ = knn.exact(Xd, Qd, k)
+            true = set(ti[0].cpu().tolist())
+            for ci, c in enumerate(f["c_grid"]):
+                r = knn.adaptive(Xd, Qd, k, delta, t, h=h, bound="exp", c_alpha=c, B0=16, B=16, grow=0)
+                cnt = int(r["count"][0])
+                got = set(r["idx"][0, :cnt].cpu().tolist())
+                rec[t, ci] = len(true & got) / k
+                ratio[t, ci] = int(r["evals"][0]) / (n * m)
+        q = lambda a, p: [round(float(v), 6) for v in np.percentile(a, p, axis=0)]
+        row = {"data": name, "C_alpha": list(f["c_grid"]), "recall_median": q(rec, 50), "recall_q25": q(rec, 25),
+               "recall_q75": q(rec, 75), "ratio_median": q(ratio, 50), "ratio_q25": q(ratio, 25),
+               "ratio_q75": q(ratio, 75)}
+        print(json.dumps(row), flush=True)
+        series.append(row)
+    print(json.dumps({"figure": "Section 5, Figure 2 trends (GPU path)", "n": n, "m": m, "k": k, "h": h,
+                      "delta": delta, "trials": f["trials"], "bound": "exp (Section 5)",
+                      "schedule": "B0 = B = 16 per round", "series": series}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -655,6 +735,7 @@ def main():
     ap.add_argument("--nq", type=int, default=None, help="queries per GPU (default 1024)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--sweep", action="store_true", help="run the gap-ratio precision sweep instead")
+    ap.add_argument("--figure2", action="store_true", help="run Section 5's C_alpha sweep (Figure 2 trends)")
     ap.add_argument("--sweep-gaps", dest="sweep_gaps", default=None, help="comma-separated gap ratios")
     ap.add_argument("--sweep-variants", dest="sweep_variants", default=None, help="comma-separated variant names")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=5.0)
@@ -680,6 +761,10 @@ def main():
     if args.sweep:
         if rank == 0:
             run_sweep(args)
+        return
+    if args.figure2:
+        if rank == 0:
+            run_figure2(args)
         return
 
     if args.impl == "reference":
