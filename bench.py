@@ -522,7 +522,7 @@ def run_serve(args):
     for i, (n, m) in enumerate(SERVE["datasets"]):
         n = max(4096, int(n * scale))
         X, P = synth.mixture_planted(n, m, SERVE["pool"], seed=100 + i)
-        ds = knn.Dataset(torch.from_numpy(X).cuda(), copies=("bf16",))
+        ds = knn.Dataset(torch.from_numpy(X).cuda(), copies=("bf16", "screen"))
         extra = {}
         if args.serve_shared:
             ds.share(0, copies=("bf16",))
@@ -533,11 +533,21 @@ def run_serve(args):
                              c_grid=C_GRID + [1e-5, 3e-6], extra=extra,
                              cache=os.path.join(tempfile.gettempdir(), f"knn_serve_tune_{os.getpid()}.json"))
         b = t["best"]
+        # the exact engine on the same held-out queries: the faster one serves the dataset
+        Hq = torch.from_numpy(P[:128]).cuda()
+        ds.exact(Hq, 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            ds.exact(Hq, 10)
+        torch.cuda.synchronize()
+        exact_qps = 3 * 128 / (time.perf_counter() - t0)
+        method = "exact" if (exact_qps > b["queries_per_s"] and not args.serve_adaptive_only) else "adaptive"
         cfgs.append(serve.DatasetConfig(storage="bf16", c_alpha=b["c_alpha"], B0=b["B0"], B=b["B"], grow=b["grow"],
-                                        threads=b["threads"], share=args.serve_shared))
+                                        threads=b["threads"], share=args.serve_shared, method=method))
         dss.append(ds)
         pools.append(P)
-        tunes.append({"n": n, "d": m, **b})
+        tunes.append({"n": n, "d": m, "engine": method, "exact_queries_per_s": round(exact_qps, 1), **b})
     # warm-up: one small request per dataset
     srv = serve.Server(dss, cfgs, slots=args.serve_slots, mem_budget=args.serve_mem << 30)
     srv.run(serve.poisson_requests(200.0, 0.05, pools, max_queries=8, seed=7)[:8])
@@ -742,6 +752,8 @@ def main():
     ap.add_argument("--serve-scale", dest="serve_scale", type=float, default=1.0)
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
     ap.add_argument("--serve-mem", dest="serve_mem", type=int, default=24, help="GiB for in-flight round state")
+    ap.add_argument("--serve-adaptive-only", dest="serve_adaptive_only", action="store_true",
+                    help="serve every dataset with the adaptive rounds (no exact engine)")
     ap.add_argument("--serve-per-pair", dest="serve_shared", action="store_false",
                     help="draw coordinates per (query, point) pair instead of shared coordinates")
     args = ap.parse_args()

@@ -133,17 +133,24 @@ __global__ void __launch_bounds__(256) screen_sgemm_kernel(const float* __restri
 }
 
 // Per query: k-th smallest screened value, then every point within 2 E_q of
-// it into cand[q, 0..kExactCand) (-1 padded); a row that does not fit is
-// marked -2 (rerank then scans every point). E_q is the screen's error bound
+// it into cand[q, 0..kExactCand) (-1 padded). E_q is the screen's error bound
 // for the query: c_cross ||x||max ||q|| + c_square (||x||max + ||q||)^2,
 // with the norms of the vectors the screen multiplied (FP32 sums, inflated by
-// their own rounding bound).
+// their own rounding bound). When that window holds more points than the
+// list (clustered data: the bound scales with the norms, not with the
+// distances), a second screen takes the window's distances directly in FP32,
+// sum of (x_j - q_j)^2, whose error is at most rel = gamma_(m+4) times the
+// distance itself: with tau32 the k-th smallest of them, every point whose
+// distance is at most the k-th true one has d32 <= tau32 (1 + rel)/(1 - rel).
+// A row that still does not fit is marked -2 (rerank then scans every point).
 constexpr int kSelNT = 512;
 
-__global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __restrict__ D, int64_t n, int m, int k,
+__global__ void __launch_bounds__(kSelNT) screen_select_kernel(float* __restrict__ D, int64_t n, int m, int k,
                                                                const float* __restrict__ qn,
                                                                const unsigned* __restrict__ xn_max_bits,
                                                                float c_cross, float c_square,
+                                                               const float* __restrict__ X,
+                                                               const float* __restrict__ Q,
                                                                int64_t* __restrict__ cand) {
   __shared__ uint32_t hist[kHistBins];
   __shared__ uint32_t buf[kSelCap];
@@ -151,7 +158,7 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __re
   __shared__ SelectShared ss;
   __shared__ int cnt;
   const int q = blockIdx.x;
-  const float* dr = D + (size_t)q * n;
+  float* dr = D + (size_t)q * n;
   for (int i = threadIdx.x; i < kHistBins; i += kSelNT) hist[i] = 0;
   __syncthreads();
   for (int64_t i = threadIdx.x; i < n; i += kSelNT) atomicAdd(&hist[f2key(__ldg(dr + i)) >> 20], 1u);
@@ -176,7 +183,55 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __re
     }
   }
   __syncthreads();
-  const int c = cnt;
+  int c = cnt;
+  if (c > kExactCand) {
+    // second screen: direct FP32 distances of the window, one warp per point
+    // (the screened row is scratch: window points get d32, the others +inf)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* qr = Q + (size_t)q * m;
+    for (int i = threadIdx.x; i < kHistBins; i += kSelNT) hist[i] = 0;
+    __syncthreads();
+    for (int64_t base = (int64_t)warp * 32; base < n; base += (int64_t)(kSelNT / 32) * 32) {
+      const int64_t i = base + lane;
+      const bool win = i < n && dr[i] <= thr;
+      unsigned bal = __ballot_sync(0xffffffffu, win);
+      if (i < n && !win) {
+        dr[i] = INFINITY;
+        atomicAdd(&hist[f2key(INFINITY) >> 20], 1u);
+      }
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const float* xr = X + (size_t)(base + src) * m;
+        float acc = 0.0f;
+        for (int j = lane; j < m; j += 32) {
+          const float t = __ldg(xr + j) - __ldg(qr + j);
+          acc = fmaf(t, t, acc);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == src) {
+          dr[i] = acc;
+          atomicAdd(&hist[f2key(acc) >> 20], 1u);
+        }
+      }
+    }
+    __syncthreads();
+    select_smallest<kSelNT>([&](int i) { return f2key(dr[i]); }, (int)n, k, hist, buf, ss, bs);
+    const float tau32 = key2f(buf[k - 1]);
+    const float rel = (float)(m + 4) * u / (1.0f - (float)(m + 4) * u);
+    const float thr2 = tau32 * ((1.0f + rel) / (1.0f - rel)) * (1.0f + 4.0f * u);
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += kSelNT) {
+      if (dr[i] <= thr2) {
+        const int p = atomicAdd(&cnt, 1);
+        if (p < kExactCand) cr[p] = i;
+      }
+    }
+    __syncthreads();
+    c = cnt;
+  }
   if (c > kExactCand) {
     for (int t = threadIdx.x; t < kExactCand; t += kSelNT) cr[t] = t == 0 ? -2 : -1;
   } else {
@@ -184,11 +239,11 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(const float* __re
   }
 }
 
-knn_status launch_screen_select(const float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
-                                const unsigned* xn_max_bits, double c_cross, double c_square, int64_t* cand,
-                                cudaStream_t stream) {
-  screen_select_kernel<<<nq, kSelNT, 0, stream>>>(D, n, m, k, qn, xn_max_bits, (float)c_cross, (float)c_square,
-                                                  cand);
+knn_status launch_screen_select(float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
+                                const unsigned* xn_max_bits, double c_cross, double c_square, const float* X,
+                                const float* Q, int64_t* cand, cudaStream_t stream) {
+  screen_select_kernel<<<nq, kSelNT, 0, stream>>>(D, n, m, k, qn, xn_max_bits, (float)c_cross, (float)c_square, X,
+                                                  Q, cand);
   return cuda_check(cudaGetLastError(), "screen_select_kernel launch");
 }
 
@@ -263,7 +318,8 @@ extern "C" knn_status knn_exact(const float* X, int64_t n, int32_t m, const floa
     dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((nq + kBN - 1) / kBN));
     screen_sgemm_kernel<<<grid, 256, 0, stream>>>(X, Q, n, nq, m, c.xn, c.qn, c.D);
     s = cuda_check(cudaGetLastError(), "exact kernels launch");
-    if (s == KNN_OK) s = launch_screen_select(c.D, n, nq, m, k, c.qn, c.xmax, 0.0, simt_c_square(m), c.cand, stream);
+    if (s == KNN_OK)
+      s = launch_screen_select(c.D, n, nq, m, k, c.qn, c.xmax, 0.0, simt_c_square(m), X, Q, c.cand, stream);
   }
   if (s == KNN_OK) s = launch_rerank(X, n, m, Q, nq, c.cand, kExactCand, k, out_idx, out_dist, stream);
   ws.release();

@@ -33,8 +33,9 @@ namespace knn {
 
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream);
-knn_status launch_screen_select(const float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
-                                const unsigned* xn_max_bits, double c_cross, double c_square, int64_t* cand,
+knn_status launch_screen_select(float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
+                                const unsigned* xn_max_bits, double c_cross, double c_square, const float* X,
+                                const float* Q, int64_t* cand,
                                 cudaStream_t stream);
 constexpr int kExactCandTc = 2048;
 
@@ -427,7 +428,7 @@ knn_status exact_tc(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k
     const double gm = (double)(m + 2) * u / (1.0 - (double)(m + 2) * u);
     const double c_cross = 1.5 * 2.0 * (gacc + 3.1 * 64.0 * u) * 1.01;
     const double c_square = 1.5 * (gm + 6.0 * u);
-    s = launch_screen_select(c.D, n, nq, m, k, c.qn, ds->xcn_max, c_cross, c_square, c.cand, stream);
+    s = launch_screen_select(c.D, n, nq, m, k, c.qn, ds->xcn_max, c_cross, c_square, ds->X, Q, c.cand, stream);
   }
   if (s == KNN_OK) s = launch_rerank(ds->X, n, m, Q, nq, c.cand, kExactCandTc, k, out_idx, out_dist, stream);
   ws.release();

@@ -2,7 +2,10 @@
 batched onto the GPU.
 
 A request holds 1..many query rows (pinned host memory), its k and the
-dataset it targets. The scheduler keeps a FIFO of arrived requests and a few
+dataset it targets. Each resident dataset is served by the engine its
+configuration names: the adaptive rounds (the default) or the exact method
+(tensor-core screen + FP64 rerank), whichever the autotuner found faster at
+the recall target for that dataset. The scheduler keeps a FIFO of arrived requests and a few
 in-flight slots, each with its own CUDA stream. Whenever a slot is free it
 takes the dataset of the oldest waiting request and packs as many waiting
 requests of that dataset as fit the batch limit and the device-memory budget
@@ -66,6 +69,7 @@ class DatasetConfig:
     threads: int = 512
     bound: str = "exp"
     share: bool = False      # shared coordinates: both Philox masks zero, column-permuted copy
+    method: str = "adaptive"  # or "exact": screen GEMM + select + FP64 rerank (k_max of the batch)
 
 
 class Server:
@@ -101,6 +105,8 @@ class Server:
         return o
 
     def _state_bytes(self, d, nq, k_max):
+        if self.configs[d].method == "exact":
+            return self.datasets[d].exact_workspace_size(nq)
         return self.datasets[d].multi_workspace_size(nq, k_max, **self._opts(d))
 
     def _admit(self, slot: _Slot) -> bool:
@@ -143,9 +149,13 @@ class Server:
             ks_d = ks.to(dev, non_blocking=False)
             qids_d = qids.to(dev, non_blocking=False)
             ws = torch.empty(need, dtype=torch.uint8, device=dev)
-            res = ds.adaptive_multi(Qd, ks_d, k_max, qids_d, self.delta, self.seed, storage=cfg.storage,
-                                    workspace=ws, stream=slot.stream, **self._opts(d))
-            ri, rd = knn.rerank(ds.X, Qd, res["idx"], k_max, stream=slot.stream)
+            if cfg.method == "exact":
+                res = None
+                ri, rd = ds.exact(Qd, k_max, workspace=ws, stream=slot.stream)
+            else:
+                res = ds.adaptive_multi(Qd, ks_d, k_max, qids_d, self.delta, self.seed, storage=cfg.storage,
+                                        workspace=ws, stream=slot.stream, **self._opts(d))
+                ri, rd = knn.rerank(ds.X, Qd, res["idx"], k_max, stream=slot.stream)
             slot.hidx = torch.empty(ri.shape, dtype=torch.int64, pin_memory=True)
             slot.hdist = torch.empty(rd.shape, dtype=torch.float64, pin_memory=True)
             slot.hidx.copy_(ri, non_blocking=True)

@@ -177,23 +177,30 @@ def mixture_planted(n: int, m: int, npool: int, centres: int = 64, sigma_frac: f
     coordinate with s = sigma_frac times the centres' per-coordinate spread
     (1); a pool of `npool` queries is drawn from the mixture and each gets
     `kplant` planted rows at distance D_far / g, g ~ U[gap_lo, gap_hi] and
-    D_far the query's median distance to `dfar_sample` rows.
+    D_far the query's median distance to `dfar_sample` rows of its own
+    cluster (the points that compete with the planted ones, so g is the ratio
+    of the competitors' distance to the planted neighbours' distance).
     Returns (X [n,m] f32, pool [npool,m] f32)."""
     g = _rng(seed)
     C = g.standard_normal((centres, m))
     X = np.empty((n, m), dtype=np.float32)
+    lab = np.empty(n, dtype=np.int64)
     step = 1 << 15
     for s in range(0, n, step):
         e = min(n, s + step)
         c = g.integers(0, centres, size=e - s)
+        lab[s:e] = c
         X[s:e] = (C[c] + sigma_frac * g.standard_normal((e - s, m))).astype(np.float32)
     c = g.integers(0, centres, size=npool)
     P = (C[c] + sigma_frac * g.standard_normal((npool, m))).astype(np.float32)
     if npool * kplant > n:
         raise ValueError("not enough rows to plant")
     rows = g.permutation(n)[: npool * kplant].reshape(npool, kplant)
+    members = [np.flatnonzero(lab == j) for j in range(centres)]
     for qi in range(npool):
-        probe = X[g.integers(0, n, size=dfar_sample)].astype(np.float64)
+        own = members[c[qi]]
+        pick = own[g.integers(0, len(own), size=dfar_sample)] if len(own) else g.integers(0, n, size=dfar_sample)
+        probe = X[pick].astype(np.float64)
         dfar = float(np.median(np.sqrt(((probe - P[qi].astype(np.float64)) ** 2).sum(axis=1))))
         r = dfar / g.uniform(gap_lo, gap_hi)
         u = g.standard_normal((kplant, m))

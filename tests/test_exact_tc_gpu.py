@@ -40,3 +40,22 @@ def test_tc_exact_gaussian_and_integer_data():
         oi, od = oracle.exact_knn(X, Q, gi.shape[1])
         np.testing.assert_array_equal(gi.cpu().numpy(), oi)
     assert knn.device_status() == 0
+
+
+def test_clustered_data_far_from_the_origin_takes_the_second_screen():
+    """Tight clusters far from the centre: the screen's bound scales with the
+    norms, so its window holds most of a cluster (more than the candidate
+    list); the direct FP32 second screen must still return the exact k
+    nearest (SIMT and tensor-core screens)."""
+    g = np.random.default_rng(5)
+    m, n, nq = 192, 24000, 12
+    C = g.normal(0.0, 30.0, size=(3, m))
+    X = (C[g.integers(0, 3, size=n)] + 0.05 * g.standard_normal((n, m))).astype(np.float32)
+    Q = (C[g.integers(0, 3, size=nq)] + 0.05 * g.standard_normal((nq, m))).astype(np.float32)
+    oi, od = oracle.exact_knn(X, Q, 10)
+    with knn.Dataset(_cuda(X), copies=("screen",)) as ds:
+        for screen in ("bf16x3", "f32"):
+            gi, gd = ds.exact(_cuda(Q), 10, screen=screen)
+            np.testing.assert_array_equal(gi.cpu().numpy(), oi)
+            np.testing.assert_allclose(gd.cpu().numpy(), od, rtol=1e-12)
+    assert knn.device_status() == 0

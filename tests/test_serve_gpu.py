@@ -16,8 +16,8 @@ pytestmark = pytest.mark.gpu
 def two_datasets():
     A, PA = synth.mixture_planted(20000, 128, 64, seed=1)
     B, PB = synth.mixture_planted(15000, 96, 64, seed=2)
-    dA = knn.Dataset(torch.from_numpy(A).cuda(), copies=("bf16",))
-    dB = knn.Dataset(torch.from_numpy(B).cuda(), copies=("bf16",))
+    dA = knn.Dataset(torch.from_numpy(A).cuda(), copies=("bf16", "screen"))
+    dB = knn.Dataset(torch.from_numpy(B).cuda(), copies=("bf16", "screen"))
     yield (dA, dB), (PA, PB), (A, B)
     dA.close()
     dB.close()
@@ -44,21 +44,29 @@ def test_mixed_launch_equals_each_query_alone(two_datasets):
 
 def test_mixed_launch_replays_in_the_oracle(two_datasets):
     """Per-query k: every query of a mixed launch follows the oracle's rounds
-    for its own k and query id (decisions and evaluation counts)."""
+    for its own k and query id. The mixed row must equal the query's solo run
+    with its decision log, which is replayed in the oracle (decisions,
+    evaluation counts, sums)."""
     (dA, _), (PA, _), (A, _) = two_datasets
     ks = np.array([1, 5, 17, 2, 9, 30], dtype=np.int32)
     qids = np.array([5, 99, 3, 12345, 7, 8], dtype=np.int64)
     Q = PA[10:16].copy()
-    r = dA.adaptive_multi(torch.from_numpy(Q).cuda(), torch.from_numpy(ks).cuda(), 30,
-                          torch.from_numpy(qids).cuda(), 0.01, 1, storage="f32", bound="exp", c_alpha=3e-3)
+    Qd = torch.from_numpy(Q).cuda()
+    opt = dict(bound="exp", c_alpha=3e-3, B0=16, B=16, grow=0)
+    r = dA.adaptive_multi(Qd, torch.from_numpy(ks).cuda(), 30, torch.from_numpy(qids).cuda(), 0.01, 1,
+                          storage="f32", **opt)
     for q in range(6):
-        p = oracle.make_params(int(ks[q]), delta=0.01, bound="exp", c_alpha=3e-3, B0=16, B=16, grow=0, seed=1,
-                               qid=int(qids[q]))
-        o = oracle.adaptive(A, Q[q:q + 1], p, want_state=False)
+        solo = dA.adaptive(Qd[q:q + 1], int(ks[q]), 0.01, 1, storage="f32", trace=True, qid_base=int(qids[q]), **opt)
+        c = int(solo["count"][0])
+        assert int(r["count"][q]) == c and int(r["evals"][q]) == int(solo["evals"][0])
+        assert torch.equal(r["idx"][q, :c], solo["idx"][0, :c])
+        p = oracle.make_params(int(ks[q]), delta=0.01, seed=1, qid=int(qids[q]), tol=1e-5, **opt)
+        code = solo["code"].cpu().numpy()
+        o = oracle.adaptive(A, Q[q:q + 1], p, replay=code)
         st = o["stats"][0]
-        assert int(r["evals"][q]) == st["evals"] and int(r["count"][q]) == st["count"]
-        c = st["count"]
-        assert set(r["idx"][q, :c].tolist()) == set(o["idx"][0, :c].tolist())
+        assert st["mismatch"] == 0 and st["log_inconsistent"] == 0, (q, st)
+        np.testing.assert_array_equal(o["code"][0], code[0])
+        assert int(solo["evals"][0]) == st["evals"] and c == st["count"]
 
 
 def _requests(pools, n, seed):
@@ -131,3 +139,28 @@ def test_shared_coordinate_serving_same_alone_and_in_the_mix(two_datasets):
     for r in done:
         a = alone[r.rid]
         assert torch.equal(r.idx, a.idx) and torch.equal(r.dist, a.dist), r.rid
+
+
+def test_exact_engine_dataset_in_the_mix(two_datasets):
+    """One dataset served by the exact engine, the other by the adaptive
+    rounds: every request gets the exact k nearest of its dataset (the oracle's
+    brute force) for the exact one, and the same result alone and mixed."""
+    dss, pools, raw = two_datasets
+    cfg = [serve.DatasetConfig(method="exact"), serve.DatasetConfig(storage="f32", c_alpha=1e-3)]
+    reqs = _requests(pools, 14, seed=21)
+    alone = {}
+    for r in reqs:
+        s = serve.Server(dss, cfg, slots=1)
+        rr = _clone(r)
+        s.submit(rr)
+        s.drain()
+        alone[r.rid] = rr
+    s = serve.Server(dss, cfg, slots=3, max_batch=96)
+    done = s.run([(0.0004 * i, _clone(r)) for i, r in enumerate(reqs)])
+    assert len(done) == len(reqs)
+    for r in done:
+        a = alone[r.rid]
+        assert torch.equal(r.idx, a.idx) and torch.equal(r.dist, a.dist), r.rid
+        if r.dataset == 0:
+            oi, _ = oracle.exact_knn(raw[0], r.Q.numpy(), r.k)
+            np.testing.assert_array_equal(r.idx.numpy(), oi)
