@@ -49,8 +49,8 @@ RECALL_TARGET = 0.999
 # capture of the timed configuration. It is
 # reported only while the kernel sources hash to the recorded value and the
 # launch configuration matches; otherwise the roofline's traffic is null.
-TRAFFIC_CAPTURE = {"sha1": "b8740c1f54b6308c074f407437a0da6ec4ce60ef",
-                   "bytes": (318e6 + 355e6) + (21.06e9 + 1.11e9),
+TRAFFIC_CAPTURE = {"sha1": "f96497e7fe033e9dd7bafd6480155e67844e9cbc",
+                   "bytes": (0.321e9 + 0.367e9) + (21.33e9 + 1.53e9),
                    "config": {"c_alpha": 1e-3, "B0": 8, "B": 8, "grow": 1, "threads": 1024, "nq": 1024}}
 
 
@@ -730,6 +730,38 @@ def run_figure2(args):
                       "schedule": "B0 = B = 16 per round", "series": series}), flush=True)
 
 
+def run_profile_step(args):
+    """The timed step alone, for profilers: the benchmark workload with the
+    options given on the command line (no autotuning, no variants), W
+    warm-up steps then K steps of the CUDA graph (rounds + rerank)."""
+    import torch
+    from paper_1902_09465_gb300 import knn, runtime
+
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    X, Q, _ = make_inputs(0)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    ds = knn.Dataset(Xd, copies=() if args.storage == "f32" else (args.storage,))
+    opts = dict(bound="exp", c_alpha=args.c_alpha or 1e-3, B0=args.B0, B=args.B, grow=args.grow, threads=args.threads,
+                block=args.block)
+    if args.share:
+        ds.share(0, copies=(args.storage,))
+        opts.update(share_points=True, share_queries=True)
+    step = runtime.GraphStep(ds, Qd.shape[0], w["k"], w["delta"], 0, storage=args.storage, **opts)
+    for _ in range(args.warmup):
+        step.run(Qd)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        res, ri, rd = step.run(Qd)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_step": w["name"], "storage": args.storage, "shared": args.share, **opts,
+                      "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 4),
+                      "evals": int(res["evals"].sum().item())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -746,6 +778,12 @@ def main():
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
     ap.add_argument("--sweep", action="store_true", help="run the gap-ratio precision sweep instead")
     ap.add_argument("--figure2", action="store_true", help="run Section 5's C_alpha sweep (Figure 2 trends)")
+    ap.add_argument("--profile-step", dest="profile_step", action="store_true",
+                    help="only the timed step with the given options (for profilers)")
+    ap.add_argument("--threads", type=int, default=1024)
+    ap.add_argument("--block", type=int, default=1)
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--share", action="store_true", help="shared coordinates (both counter masks zero)")
     ap.add_argument("--sweep-gaps", dest="sweep_gaps", default=None, help="comma-separated gap ratios")
     ap.add_argument("--sweep-variants", dest="sweep_variants", default=None, help="comma-separated variant names")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=5.0)
@@ -777,6 +815,10 @@ def main():
     if args.figure2:
         if rank == 0:
             run_figure2(args)
+        return
+    if args.profile_step:
+        if rank == 0:
+            run_profile_step(args)
         return
 
     if args.impl == "reference":
