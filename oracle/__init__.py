@@ -75,6 +75,8 @@ def lib():
             L.orc_sequential.argtypes = [P, C.c_int64, C.c_int32, P, C.POINTER(AdaptiveParams), C.c_int64,
                                          P, P, P]
             L.orc_sequential.restype = C.c_int32
+            L.orc_sequential_heaps.argtypes = L.orc_sequential.argtypes
+            L.orc_sequential_heaps.restype = C.c_int32
             L.orc_max_threads.restype = C.c_int32
             L.orc_quantize.argtypes = [C.c_int32, P, C.c_int64, C.c_int32, P, P]
             L.orc_quantize.restype = C.c_double
@@ -171,8 +173,10 @@ def adaptive(X, Q, params: AdaptiveParams, replay=None, want_state=True, threads
     return {"idx": idx, "code": code, "S": S, "T": T, "stats": [s.as_dict() for s in st]}
 
 
-def sequential(X, q, params: AdaptiveParams, max_iter=None):
-    """Algorithm 1 as printed, one query. Returns (idx [k+h], evals, iters)."""
+def sequential(X, q, params: AdaptiveParams, max_iter=None, heaps=False):
+    """Algorithm 1 as printed, one query. Returns (idx [k+h], evals, iters).
+    heaps=True runs the seven-heap implementation (Section 4.1), O(log n)
+    per iteration; the default scans the sets, O(n) per iteration."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     q = np.ascontiguousarray(np.ravel(q), dtype=np.float32)
     n, m = X.shape
@@ -182,8 +186,8 @@ def sequential(X, q, params: AdaptiveParams, max_iter=None):
     it = np.zeros(1, dtype=np.int64)
     if max_iter is None:
         max_iter = 4 * n * m + 16
-    rc = lib().orc_sequential(_ptr(X), n, m, _ptr(q), C.byref(params), int(max_iter), _ptr(idx), _ptr(ev),
-                              _ptr(it))
+    fn = lib().orc_sequential_heaps if heaps else lib().orc_sequential
+    rc = fn(_ptr(X), n, m, _ptr(q), C.byref(params), int(max_iter), _ptr(idx), _ptr(ev), _ptr(it))
     if rc == 1:
         raise ValueError("oracle rejected the arguments")
     return idx, int(ev[0]), int(it[0])

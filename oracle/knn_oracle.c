@@ -597,3 +597,238 @@ int32_t orc_sequential(const float* X, int64_t n, int32_t m, const float* q,
     free(sum); free(est); free(al); free(Tn); free(perm);
     return it >= max_iter ? 2 : 0;
 }
+
+/* ----------------------------------------- Algorithm 1 with the seven heaps */
+
+/* The same algorithm as orc_sequential, with the data structures of Section
+ * 4.1 (Figure "heaps"): the points are split by their rank in the (estimate,
+ * index) order into the close set (ranks 1..k), the middle set (k+1..k+h)
+ * and the far set (the rest). Close keeps a max-heap on the estimate and a
+ * max-heap on the UCB (q1 is its top); middle a min- and a max-heap on the
+ * estimate and a max-heap on the width (candidates for b2); far a min-heap
+ * on the estimate and a min-heap on the LCB (q2 is its top). An iteration
+ * costs O(log n): the two updated points leave their heaps, are re-inserted,
+ * and the sets are repaired by swapping boundary elements. Ties follow the
+ * rank order, as in the scan version. */
+
+enum { HC_EST = 0, HC_UCB, HM_EMIN, HM_EMAX, HM_AL, HF_EST, HF_LCB, NHEAP };
+
+typedef struct {
+    const double* est;
+    const double* al;
+    int64_t* a[NHEAP];
+    int64_t* pos[NHEAP];
+    int64_t size[NHEAP];
+} heaps_t;
+
+static int rank_lt(const heaps_t* H, int64_t i, int64_t j) {
+    return H->est[i] < H->est[j] || (H->est[i] == H->est[j] && i < j);
+}
+
+/* 1 if i belongs above j in heap t */
+static int heap_before(const heaps_t* H, int t, int64_t i, int64_t j) {
+    const double* e = H->est;
+    const double* a = H->al;
+    switch (t) {
+    case HC_EST: case HM_EMAX: return rank_lt(H, j, i);
+    case HM_EMIN: case HF_EST: return rank_lt(H, i, j);
+    case HC_UCB: {
+        double ui = e[i] + a[i], uj = e[j] + a[j];
+        return ui > uj || (ui == uj && rank_lt(H, i, j));
+    }
+    case HM_AL: return a[i] > a[j] || (a[i] == a[j] && rank_lt(H, i, j));
+    default: { /* HF_LCB */
+        double li = e[i] - a[i], lj = e[j] - a[j];
+        return li < lj || (li == lj && rank_lt(H, i, j));
+    }
+    }
+}
+
+static void heap_swap(heaps_t* H, int t, int64_t x, int64_t y) {
+    int64_t* a = H->a[t];
+    int64_t v = a[x];
+    a[x] = a[y]; a[y] = v;
+    H->pos[t][a[x]] = x;
+    H->pos[t][a[y]] = y;
+}
+
+static void heap_sift(heaps_t* H, int t, int64_t x) {
+    int64_t* a = H->a[t];
+    while (x > 0 && heap_before(H, t, a[x], a[(x - 1) / 2])) {
+        heap_swap(H, t, x, (x - 1) / 2);
+        x = (x - 1) / 2;
+    }
+    for (;;) {
+        int64_t l = 2 * x + 1, r = l + 1, b = x;
+        if (l < H->size[t] && heap_before(H, t, a[l], a[b])) b = l;
+        if (r < H->size[t] && heap_before(H, t, a[r], a[b])) b = r;
+        if (b == x) break;
+        heap_swap(H, t, x, b);
+        x = b;
+    }
+}
+
+static void heap_push(heaps_t* H, int t, int64_t i) {
+    int64_t x = H->size[t]++;
+    H->a[t][x] = i;
+    H->pos[t][i] = x;
+    heap_sift(H, t, x);
+}
+
+static void heap_remove(heaps_t* H, int t, int64_t i) {
+    int64_t x = H->pos[t][i], last = --H->size[t];
+    if (x != last) {
+        heap_swap(H, t, x, last);
+        H->pos[t][i] = -1;
+        heap_sift(H, t, x);
+    } else {
+        H->pos[t][i] = -1;
+    }
+}
+
+static const int set_heaps[3][3] = {{HC_EST, HC_UCB, -1}, {HM_EMIN, HM_EMAX, HM_AL}, {HF_EST, HF_LCB, -1}};
+
+static void set_insert(heaps_t* H, unsigned char* set, int s, int64_t i) {
+    set[i] = (unsigned char)s;
+    for (int u = 0; u < 3; ++u)
+        if (set_heaps[s][u] >= 0) heap_push(H, set_heaps[s][u], i);
+}
+
+static void set_remove(heaps_t* H, const unsigned char* set, int64_t i) {
+    for (int u = 0; u < 3; ++u)
+        if (set_heaps[set[i]][u] >= 0) heap_remove(H, set_heaps[set[i]][u], i);
+}
+
+/* Restores close < middle < far in the (estimate, index) order by swapping
+ * the offending boundary elements. */
+static void sets_repair(heaps_t* H, unsigned char* set, int32_t h) {
+    for (;;) {
+        int changed = 0;
+        if (h > 0) {
+            int64_t c = H->a[HC_EST][0], mm = H->a[HM_EMIN][0];
+            if (rank_lt(H, mm, c)) {
+                set_remove(H, set, c); set_remove(H, set, mm);
+                set_insert(H, set, 1, c); set_insert(H, set, 0, mm);
+                changed = 1;
+            }
+            int64_t mx = H->a[HM_EMAX][0], f = H->a[HF_EST][0];
+            if (rank_lt(H, f, mx)) {
+                set_remove(H, set, mx); set_remove(H, set, f);
+                set_insert(H, set, 2, mx); set_insert(H, set, 1, f);
+                changed = 1;
+            }
+        } else {
+            int64_t c = H->a[HC_EST][0], f = H->a[HF_EST][0];
+            if (rank_lt(H, f, c)) {
+                set_remove(H, set, c); set_remove(H, set, f);
+                set_insert(H, set, 2, c); set_insert(H, set, 0, f);
+                changed = 1;
+            }
+        }
+        if (!changed) break;
+    }
+}
+
+static int cmp_rank_pair(const void* x, const void* y) {
+    const vi_t* a = (const vi_t*)x;
+    const vi_t* b = (const vi_t*)y;
+    if (a->v < b->v) return -1;
+    if (a->v > b->v) return 1;
+    return (a->i > b->i) - (a->i < b->i);
+}
+
+int32_t orc_sequential_heaps(const float* X, int64_t n, int32_t m, const float* q,
+                             const orc_adaptive_params* p, int64_t max_iter,
+                             int64_t* out_idx, int64_t* out_evals, int64_t* out_iters) {
+    const int32_t k = p->k, h = p->h;
+    const int64_t kh = (int64_t)k + h;
+    if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0)) return 1;
+    for (int64_t t = 0; t < kh; ++t) out_idx[t] = -1;
+    *out_evals = 0;
+    *out_iters = 0;
+    if (n <= kh) {
+        for (int64_t i = 0; i < n; ++i) out_idx[i] = i;
+        return 0;
+    }
+    double lo = q[0], hi = q[0];
+    for (int32_t j = 0; j < m; ++j) { if (q[j] < lo) lo = q[j]; if (q[j] > hi) hi = q[j]; }
+    for (size_t e = 0; e < (size_t)n * (size_t)m; ++e) { if (X[e] < lo) lo = X[e]; if (X[e] > hi) hi = X[e]; }
+    const double span2 = (hi - lo) * (hi - lo);
+
+    double* sum = (double*)malloc(sizeof(double) * (size_t)n);
+    double* est = (double*)malloc(sizeof(double) * (size_t)n);
+    double* al = (double*)malloc(sizeof(double) * (size_t)n);
+    int64_t* Tn = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+    unsigned char* set = (unsigned char*)malloc((size_t)n);
+    vi_t* order = (vi_t*)malloc(sizeof(vi_t) * (size_t)n);
+    heaps_t H;
+    H.est = est;
+    H.al = al;
+    for (int t = 0; t < NHEAP; ++t) {
+        H.a[t] = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        H.pos[t] = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        H.size[t] = 0;
+        for (int64_t i = 0; i < n; ++i) H.pos[t][i] = -1;
+    }
+    int64_t evals = 0;
+    /* Initialisation: one sample per point (as the scan version). */
+    for (int64_t i = 0; i < n; ++i) {
+        const float* xi = X + (size_t)i * (size_t)m;
+        if (m == 1) {
+            sum[i] = sqdist(xi, q, m); Tn[i] = 1; est[i] = sum[i]; al[i] = 0.0; evals += 1;
+        } else {
+            int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)i, 0, m, p->mask_p, p->mask_q);
+            double d = (double)xi[j] - (double)q[j];
+            sum[i] = d * d; Tn[i] = 1; est[i] = sum[i];
+            al[i] = span2 * orc_alpha(p->bound, p->c_alpha, 1, n, p->delta);
+            evals += 1;
+        }
+        order[i].v = est[i];
+        order[i].i = i;
+    }
+    qsort(order, (size_t)n, sizeof(vi_t), cmp_rank_pair);
+    for (int64_t r = 0; r < n; ++r) set_insert(&H, set, r < k ? 0 : (r < kh ? 1 : 2), order[r].i);
+    int64_t it = 0;
+    for (; it < max_iter; ++it) {
+        const int64_t q1 = H.a[HC_UCB][0], q2 = H.a[HF_LCB][0];
+        if (est[q1] + al[q1] <= est[q2] - al[q2]) break; /* Eq. termination */
+        int64_t b2 = q2;
+        if (h > 0) {
+            const int64_t c = H.a[HM_AL][0];
+            if (al[c] > al[q2]) b2 = c;
+        }
+        const int64_t upd[2] = {q1, b2};
+        for (int u = 0; u < 2; ++u) {
+            const int64_t l = upd[u];
+            if (Tn[l] >= m) continue;
+            const int s = set[l];
+            set_remove(&H, set, l);
+            const float* xl = X + (size_t)l * (size_t)m;
+            int32_t j = orc_coordinate(p->seed, p->qid, (uint64_t)l, (uint64_t)Tn[l], m, p->mask_p, p->mask_q);
+            double d = (double)xl[j] - (double)q[j];
+            sum[l] += d * d;
+            Tn[l] += 1;
+            evals += 1;
+            if (Tn[l] == m) {
+                est[l] = sqdist(xl, q, m) / (double)m;
+                al[l] = 0.0;
+                evals += m;
+            } else {
+                est[l] = sum[l] / (double)Tn[l];
+                al[l] = span2 * orc_alpha(p->bound, p->c_alpha, Tn[l], n, p->delta);
+            }
+            set_insert(&H, set, s, l);
+        }
+        sets_repair(&H, set, h);
+    }
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (set[i] != 2) { order[cnt].v = est[i]; order[cnt].i = i; ++cnt; }
+    qsort(order, (size_t)cnt, sizeof(vi_t), cmp_rank_pair);
+    for (int64_t t = 0; t < cnt && t < kh; ++t) out_idx[t] = order[t].i;
+    *out_evals = evals;
+    *out_iters = it;
+    for (int t = 0; t < NHEAP; ++t) { free(H.a[t]); free(H.pos[t]); }
+    free(sum); free(est); free(al); free(Tn); free(set); free(order);
+    return it >= max_iter ? 2 : 0;
+}

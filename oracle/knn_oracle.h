@@ -102,6 +102,12 @@ int32_t orc_sequential(const float* X, int64_t n, int32_t m, const float* q,
                        const orc_adaptive_params* p, int64_t max_iter,
                        int64_t* out_idx, int64_t* out_evals, int64_t* out_iters);
 
+/* Algorithm 1 with the seven heaps of Section 4.1 (Figure "heaps"): the same
+ * iterations, samples and output as orc_sequential, O(log n) per iteration. */
+int32_t orc_sequential_heaps(const float* X, int64_t n, int32_t m, const float* q,
+                             const orc_adaptive_params* p, int64_t max_iter,
+                             int64_t* out_idx, int64_t* out_evals, int64_t* out_iters);
+
 /* Brute force for many queries (OpenMP). idx/dist are nq x k. */
 void orc_exact_knn_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
                          int32_t k, int64_t* idx, double* dist, int32_t threads);

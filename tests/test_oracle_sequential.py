@@ -1,0 +1,59 @@
+"""Algorithm 1 with the seven heaps of Section 4.1 against the version that
+scans the sets: the same iterations, evaluations and returned set on every
+case (the two share the sampling and the arithmetic of an iteration, and
+differ in how q1, q2 and b2 are found and the order is kept), and the
+heap version's containment of the k nearest on easy and binary data."""
+
+import time
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1902_09465_gb300 import synth
+
+
+@pytest.mark.parametrize("n,m,k,h,bound,c,seed", [
+    (300, 64, 3, 3, "exp", 1e-3, 0), (500, 128, 5, 0, "exp", 3e-4, 1), (400, 33, 1, 4, "footnote", 1.0, 2),
+    (250, 200, 10, 10, "exp", 1e-2, 3), (120, 1, 2, 2, "exp", 1e-3, 4), (600, 96, 7, 2, "lemma", 1.0, 5)])
+def test_heaps_equal_scans(n, m, k, h, bound, c, seed):
+    X, Q, _ = synth.gaussian_planted(n, m, k, seed=seed)
+    p = oracle.make_params(k, h=h, delta=0.05, bound=bound, c_alpha=c, seed=seed)
+    a = oracle.sequential(X, Q[0], p)
+    b = oracle.sequential(X, Q[0], p, heaps=True)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1:] == b[1:]
+
+
+def test_heaps_equal_scans_with_ties():
+    # duplicated rows and integer data: many equal estimates, the rank order decides
+    X, Q, _ = synth.gap_planted(400, 16, 2, 4, [3.0, 1.05], seed=7, background="int255")
+    X[50:80] = X[10]
+    for qi in range(2):
+        p = oracle.make_params(4, h=3, delta=0.05, bound="exp", c_alpha=1e-3, seed=qi)
+        a = oracle.sequential(X, Q[qi], p)
+        b = oracle.sequential(X, Q[qi], p, heaps=True)
+        np.testing.assert_array_equal(a[0], b[0])
+        assert a[1:] == b[1:]
+
+
+def test_heaps_contain_the_knn_and_scale():
+    """Theorem 1 on +-1/2 data, and a run the scan version would take far
+    longer on (n = 20,000)."""
+    fails = 0
+    for t in range(60):
+        X, q, near = synth.binary_half(150, 2048, 3, 0.05, 0.45, seed=4000 + t)
+        p = oracle.make_params(3, delta=0.05, bound="footnote", seed=t)
+        idx, ev, it = oracle.sequential(X, q, p, heaps=True)
+        ti, _ = oracle.exact_knn(X, q, 3)
+        fails += not set(ti[0]) <= set(idx.tolist())
+    assert fails <= stats.binom.ppf(0.999, 60, 0.05)
+    X, Q, _ = synth.gaussian_planted(20000, 128, 5, seed=9)
+    p = oracle.make_params(5, delta=0.01, bound="exp", c_alpha=1e-4, seed=1)
+    t0 = time.perf_counter()
+    idx, ev, it = oracle.sequential(X, Q[0], p, heaps=True)
+    assert time.perf_counter() - t0 < 30
+    ti, _ = oracle.exact_knn(X, Q, 5)
+    assert set(ti[0]) <= set(idx.tolist())
+    assert ev < 0.2 * 20000 * 128
