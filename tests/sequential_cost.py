@@ -3,9 +3,9 @@ version), both on the CPU oracle: the fraction of the naive method's
 coordinate evaluations (n m) each spends, and whether the k nearest are
 returned, on the same seeded inputs and the same bound (Section 5's form).
 
-    python oracle/compare_sequential.py
+    python tests/sequential_cost.py
 
-Test infrastructure: it runs the oracle only."""
+Test infrastructure: it runs the oracle only (inputs from the seeded generators)."""
 
 import os
 import sys
