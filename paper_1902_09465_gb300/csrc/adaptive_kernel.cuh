@@ -552,6 +552,15 @@ __device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, flo
   __syncthreads();
   select_smallest<NT>([&](int i) { return f2key(mq[i]); }, nt, k, hist, buf, sh.ss, sh.bs);
   const float tU = key2f(buf[k - 1]) / Tf + w;  // the UCB of that sum, formed as the thresholds form it
+  // The LCB fl(fl(S / T) - w) does not decrease with S, so the dropped sums
+  // are those above one float Sc: found once by bisection on the bit
+  // patterns of non-negative floats, it turns the test into one comparison.
+  uint32_t lo = 0u, hi = 0x7F800000u;  // L(0) <= tU (kept), L(+inf) > tU (dropped)
+  while (hi - lo > 1u) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if (__uint_as_float(mid) / Tf - w > tU) hi = mid; else lo = mid;
+  }
+  const float Sc = __uint_as_float(lo);
   for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
   __syncthreads();
   // warp w scans its own contiguous segment, U loads in flight per lane;
@@ -562,7 +571,7 @@ __device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, flo
   const int64_t s0 = (int64_t)warp * seg, s1 = min(n, s0 + seg);
   const float* R0q = a.R0 + (size_t)q * (size_t)n;
   int cnt = 0;
-  float mn = INFINITY;
+  float mn = INFINITY;  // smallest dropped sum
   for (int64_t base = s0; base < s1; base += 32 * U) {
     float v[U];
 #pragma unroll
@@ -575,9 +584,8 @@ __device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, flo
       const int64_t i = base + u * 32 + lane;
       bool keep = false;
       if (i < s1) {
-        const float L = v[u] / Tf - w;  // the LCB as the decide pass forms it
-        if (L > tU) {
-          mn = fminf(mn, L);
+        if (v[u] > Sc) {  // LCB > tU
+          mn = fminf(mn, v[u]);
           if (lcode) {
             lcode[i] = 1;  // eliminated in round 0
             if (lS) lS[i] = v[u];
@@ -604,7 +612,7 @@ __device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, flo
     SA[woff + t] = stS[s0 + t];
   }
   mn = block_min<NT>(mn, sh.bs);
-  *min_elim = fminf(*min_elim, mn);
+  if (mn < INFINITY) *min_elim = fminf(*min_elim, mn / Tf - w);  // the smallest dropped LCB
   return total;
 }
 
@@ -1027,7 +1035,7 @@ constexpr int kR0SharedThreads = 256;
 
 template <int NB>
 struct R0SharedCfg {
-  static constexpr int kQueries = NB <= 2 ? 256 : 64;  // queries staged at a time (16 KB)
+  static constexpr int kQueries = NB <= 2 ? 256 : (NB <= 4 ? 128 : 64);  // queries staged at a time (16 KB)
 };
 
 // The chunk's query values at the first W permuted columns (zero past B0),
@@ -1039,6 +1047,42 @@ static __global__ void permute_query_columns_kernel(const float* __restrict__ Q,
   if (e >= (int64_t)nq * W) return;
   const int q = (int)(e / W), t = (int)(e - (int64_t)q * W);
   Qp[e] = t < B0 ? __ldg(Q + (size_t)q * m + jperm[t]) : 0.0f;
+}
+
+// One point's round-0 sum against one staged query row v4 (the round loop's
+// order: blocks of 8 draws into partials, then the lane butterfly over G).
+template <int NB>
+__device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4, int nfull, int rem, int G) {
+  float p[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    p[b] = 0.0f;
+    if (b < nfull || (b == nfull && rem)) {  // uniform over the grid
+      const float4 va = v4[2 * b], vb = v4[2 * b + 1];
+      const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+      if (b < nfull) {
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const float d = x[8 * b + w] - vv[w];
+          p[b] = fmaf(d, d, p[b]);
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < 8; ++w)
+          if (w < rem) {
+            const float d = x[8 * b + w] - vv[w];
+            p[b] = fmaf(d, d, p[b]);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = NB / 2; o; o >>= 1)
+    if (o < G) {
+#pragma unroll
+      for (int j = 0; j < o; ++j) p[j] += p[j + o];
+    }
+  return p[0];
 }
 
 template <class E, int NB>
@@ -1077,38 +1121,8 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
   }
   __syncthreads();
   if (((int64_t)blockIdx.x * kR0SharedThreads + (threadIdx.x & ~31)) >= n) return;  // warp-uniform
-  for (int qq = 0; qq < qc; ++qq) {
-    const float4* v4 = reinterpret_cast<const float4*>(qv + qq * W);
-    float p[NB];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      p[b] = 0.0f;
-      if (b < nfull || (b == nfull && rem)) {  // uniform over the grid
-        const float4 va = v4[2 * b], vb = v4[2 * b + 1];
-        const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
-        if (b < nfull) {
-#pragma unroll
-          for (int w = 0; w < 8; ++w) {
-            const float d = x[8 * b + w] - vv[w];
-            p[b] = fmaf(d, d, p[b]);
-          }
-        } else {
-#pragma unroll
-          for (int w = 0; w < 8; ++w)
-            if (w < rem) {
-              const float d = x[8 * b + w] - vv[w];
-              p[b] = fmaf(d, d, p[b]);
-            }
-        }
-      }
-    }
-#pragma unroll
-    for (int o = NB / 2; o; o >>= 1)
-      if (o < G) {
-#pragma unroll
-        for (int j = 0; j < o; ++j) p[j] += p[j + o];
-      }
-    const float S = p[0];
+  const float4* v4 = reinterpret_cast<const float4*>(qv);
+  auto store = [&](int qq, float S) {
     const int qg = q0 + qq;
     if (i < n) R0[(size_t)qg * (size_t)n + i] = S;
     if (R0min) {  // smallest sum of the warp's 32 points
@@ -1117,7 +1131,15 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
       for (int o = 16; o; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
       if ((threadIdx.x & 31) == 0) R0min[(size_t)qg * (size_t)a.r0tiles + (size_t)(i >> 5)] = t;
     }
+  };
+  int qq = 0;
+  for (; qq + 1 < qc; qq += 2) {  // two queries at a time: independent chains
+    const float S0 = r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G);
+    const float S1 = r0_shared_sum<NB>(x, v4 + (size_t)(qq + 1) * (W / 4), nfull, rem, G);
+    store(qq, S0);
+    store(qq + 1, S1);
   }
+  if (qq < qc) store(qq, r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G));
 }
 
 // Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and

@@ -198,7 +198,7 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
   const int tiles = !r0 ? 0 : (int)(E::kPerm ? (n + 31) / 32 : (n + rows - 1) / rows);
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
-  const int qpw = E::kPerm && r0 ? (o.B0 <= 16 ? 16 : 64) : 0;  // permuted query columns staged by round 0
+  const int qpw = E::kPerm && r0 ? (o.B0 <= 16 ? 16 : (o.B0 <= 32 ? 32 : 64)) : 0;  // staged by round 0
   if (r0) {
     measure.take<float>((size_t)chunk * (size_t)n);
     measure.take<float>((size_t)chunk * (size_t)tiles);
@@ -312,6 +312,9 @@ static knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int3
         if (o.B0 <= 16) {
           const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<2>::kQueries - 1) / R0SharedCfg<2>::kQueries));
           round0_shared_kernel<E, 2><<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
+        } else if (o.B0 <= 32) {
+          const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<4>::kQueries - 1) / R0SharedCfg<4>::kQueries));
+          round0_shared_kernel<E, 4><<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
         } else {
           const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<8>::kQueries - 1) / R0SharedCfg<8>::kQueries));
           round0_shared_kernel<E, 8><<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
