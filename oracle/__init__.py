@@ -44,7 +44,7 @@ class AdaptiveParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double),
                 ("delta", C.c_double), ("B0", C.c_int32), ("B", C.c_int32), ("grow", C.c_int32),
                 ("seed", C.c_uint64), ("qid", C.c_uint64), ("mask_p", C.c_uint64), ("mask_q", C.c_uint64),
-                ("tol", C.c_double), ("storage", C.c_int32), ("block", C.c_int32)]
+                ("tol", C.c_double), ("storage", C.c_int32), ("block", C.c_int32), ("metric", C.c_int32)]
 
 
 class AdaptiveStats(C.Structure):
@@ -69,6 +69,8 @@ def lib():
             L.orc_alpha.argtypes = [C.c_int32, C.c_double, C.c_int64, C.c_int64, C.c_double]
             L.orc_alpha.restype = C.c_double
             L.orc_exact_knn_batch.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, C.c_int32, P, P, C.c_int32]
+            L.orc_exact_knn_batch_metric.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P,
+                                                     P, C.c_int32]
             L.orc_adaptive_batch.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, C.POINTER(AdaptiveParams),
                                              P, P, P, P, P, P, C.c_int32]
             L.orc_adaptive_batch.restype = C.c_int32
@@ -124,20 +126,25 @@ def max_threads() -> int:
     return int(lib().orc_max_threads())
 
 
-def exact_knn(X, Q, k, threads=0):
-    """Brute force (Section 3). Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+METRIC = {"l2": 0, "l1": 1}
+
+
+def exact_knn(X, Q, k, threads=0, metric="l2"):
+    """Brute force (Section 3). Returns (idx [nq,k] int64, dist [nq,k] f64):
+    squared l2 distances, or l1 distances with metric="l1"."""
     X = np.ascontiguousarray(X, dtype=np.float32)
     Q = np.ascontiguousarray(np.atleast_2d(Q), dtype=np.float32)
     n, m = X.shape
     nq = Q.shape[0]
     idx = np.empty((nq, k), dtype=np.int64)
     dist = np.empty((nq, k), dtype=np.float64)
-    lib().orc_exact_knn_batch(_ptr(X), n, m, _ptr(Q), nq, k, _ptr(idx), _ptr(dist), int(threads))
+    lib().orc_exact_knn_batch_metric(_ptr(X), n, m, _ptr(Q), nq, k, METRIC[metric], _ptr(idx), _ptr(dist),
+                                     int(threads))
     return idx, dist
 
 
 def make_params(k, h=None, delta=0.01, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, seed=0,
-                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32", block=1):
+                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32", block=1, metric="l2"):
     """Parameters of the batched rounds; `block` = coordinates per sample
     (1: single coordinates as in the paper; g > 1: blocks of g consecutive
     coordinates, B0 and B then count blocks)."""
@@ -145,7 +152,8 @@ def make_params(k, h=None, delta=0.01, bound="footnote", c_alpha=1.0, B0=16, B=1
     return AdaptiveParams(int(k), int(k if h is None else h), BOUND[bound] if isinstance(bound, str) else int(bound),
                           float(c_alpha), float(delta), int(B0), int(B), int(grow), int(seed), int(qid),
                           0 if share_points else full, 0 if share_queries else full, float(tol),
-                          STORAGE[storage] if isinstance(storage, str) else int(storage), int(block))
+                          STORAGE[storage] if isinstance(storage, str) else int(storage), int(block),
+                          METRIC[metric] if isinstance(metric, str) else int(metric))
 
 
 def adaptive(X, Q, params: AdaptiveParams, replay=None, want_state=True, threads=0):

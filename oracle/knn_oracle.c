@@ -176,11 +176,25 @@ static double sqdist(const float* x, const float* q, int32_t m) {
     return s;
 }
 
-void orc_exact_knn(const float* X, int64_t n, int32_t m, const float* q, int32_t k,
-                   int64_t* idx, double* dist) {
+/* l1 distance (the generalisation named in Section 3). */
+static double l1dist(const float* x, const float* q, int32_t m) {
+    double s = 0.0;
+    for (int32_t j = 0; j < m; ++j) s += fabs((double)x[j] - (double)q[j]);
+    return s;
+}
+
+static double dist_of(int32_t metric, const float* x, const float* q, int32_t m) {
+    return metric == ORC_METRIC_L1 ? l1dist(x, q, m) : sqdist(x, q, m);
+}
+
+/* One coordinate's contribution: (x - q)^2, or |x - q| for l1. */
+static double term_of(int32_t metric, double d) { return metric == ORC_METRIC_L1 ? fabs(d) : d * d; }
+
+void orc_exact_knn_metric(const float* X, int64_t n, int32_t m, const float* q, int32_t k, int32_t metric,
+                          int64_t* idx, double* dist) {
     vi_t* a = (vi_t*)malloc(sizeof(vi_t) * (size_t)n);
     for (int64_t i = 0; i < n; ++i) {
-        a[i].v = sqdist(X + (size_t)i * (size_t)m, q, m);
+        a[i].v = dist_of(metric, X + (size_t)i * (size_t)m, q, m);
         a[i].i = i;
     }
     qsort(a, (size_t)n, sizeof(vi_t), cmp_vi);
@@ -191,15 +205,25 @@ void orc_exact_knn(const float* X, int64_t n, int32_t m, const float* q, int32_t
     free(a);
 }
 
-void orc_exact_knn_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
-                         int32_t k, int64_t* idx, double* dist, int32_t threads) {
+void orc_exact_knn(const float* X, int64_t n, int32_t m, const float* q, int32_t k,
+                   int64_t* idx, double* dist) {
+    orc_exact_knn_metric(X, n, m, q, k, ORC_METRIC_L2SQ, idx, dist);
+}
+
+void orc_exact_knn_batch_metric(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                                int32_t k, int32_t metric, int64_t* idx, double* dist, int32_t threads) {
 #ifdef _OPENMP
     if (threads > 0) omp_set_num_threads(threads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int32_t qi = 0; qi < nq; ++qi)
-        orc_exact_knn(X, n, m, Q + (size_t)qi * (size_t)m, k, idx + (size_t)qi * (size_t)k,
-                      dist ? dist + (size_t)qi * (size_t)k : NULL);
+        orc_exact_knn_metric(X, n, m, Q + (size_t)qi * (size_t)m, k, metric, idx + (size_t)qi * (size_t)k,
+                             dist ? dist + (size_t)qi * (size_t)k : NULL);
+}
+
+void orc_exact_knn_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                         int32_t k, int64_t* idx, double* dist, int32_t threads) {
+    orc_exact_knn_batch_metric(X, n, m, Q, nq, k, ORC_METRIC_L2SQ, idx, dist, threads);
 }
 
 int32_t orc_max_threads(void) {
@@ -287,10 +311,13 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
      * |xt - x| |xt + x - 2q| <= emax (2 span + emax), so its distances lie
      * within eps of the true ones, and its samples within [0, (span + 2 emax)^2]:
      * the width of the sampled bounds grows accordingly. The exact cap reads
-     * the FP32 data, so exact distances keep width 0. */
-    const double spanw = span + 2.0 * emax;
-    const double span2 = spanw * spanw;
-    const double eps = emax * (2.0 * span + emax);
+     * the FP32 data, so exact distances keep width 0.
+     * For l1 a sample |x - q| lies in [0, span] (normalised by span, not
+     * span^2), and a copy moves it by at most emax, within [0, span + emax]. */
+    const int32_t metric = p->metric;
+    const double spanw = metric == ORC_METRIC_L1 ? span + emax : span + 2.0 * emax;
+    const double span2 = metric == ORC_METRIC_L1 ? spanw : spanw * spanw;
+    const double eps = metric == ORC_METRIC_L1 ? emax : emax * (2.0 * span + emax);
 
     unsigned char* status = (unsigned char*)malloc((size_t)n);
     double* Sx = (double*)malloc(sizeof(double) * (size_t)n);
@@ -321,16 +348,13 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
             if (status[i] != ORC_ACTIVE) continue;
             const float* xi = G + (size_t)i * (size_t)m;
             if (exact) { /* the exact distance is taken on the FP32 data itself */
-                Sx[i] = sqdist(X + (size_t)i * (size_t)m, q, m);
+                Sx[i] = dist_of(metric, X + (size_t)i * (size_t)m, q, m);
             } else {
                 for (int64_t t = Tcur; t < Tn; ++t) {
                     /* draw t picks block b: coordinates b*g .. min(b*g + g, m) - 1 */
                     int32_t b = orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, M, p->mask_p, p->mask_q);
                     int32_t j1 = (b + 1) * g < m ? (b + 1) * g : m;
-                    for (int32_t j = b * g; j < j1; ++j) {
-                        double d = (double)xi[j] - (double)q[j];
-                        Sx[i] += d * d;
-                    }
+                    for (int32_t j = b * g; j < j1; ++j) Sx[i] += term_of(metric, (double)xi[j] - (double)q[j]);
                 }
             }
             Tx[i] = (int32_t)Tn;

@@ -40,6 +40,9 @@ double orc_alpha(int32_t form, double c_alpha, int64_t u, int64_t n, double delt
  * ties broken by the smaller index. idx[k], dist[k] (squared distances). */
 void orc_exact_knn(const float* X, int64_t n, int32_t m, const float* q, int32_t k,
                    int64_t* idx, double* dist);
+/* The same under a metric (ORC_METRIC_*); dist holds that metric's values. */
+void orc_exact_knn_metric(const float* X, int64_t n, int32_t m, const float* q, int32_t k, int32_t metric,
+                          int64_t* idx, double* dist);
 
 typedef struct {
     int32_t k, h;
@@ -53,7 +56,11 @@ typedef struct {
     int32_t block;        /* coordinates per sample: 0 or 1 is the paper's one coordinate; g > 1 draws
                            * one of ceil(m/g) blocks of g consecutive coordinates (the last may be
                            * shorter) and adds the block's sum of squared differences */
+    int32_t metric;       /* ORC_METRIC_*: squared l2 (the paper's), or l1 (Section 3's generalisation):
+                           * samples |x_j - q_j|, normalised by span instead of span^2 */
 } orc_adaptive_params;
+
+enum { ORC_METRIC_L2SQ = 0, ORC_METRIC_L1 = 1 };
 
 /* Storage of the gathered copy: FP32 itself, BF16 (round to nearest even),
  * or FP8 e4m3 with a per-row scale max|x_i| / 448. */
@@ -111,6 +118,8 @@ int32_t orc_sequential_heaps(const float* X, int64_t n, int32_t m, const float* 
 /* Brute force for many queries (OpenMP). idx/dist are nq x k. */
 void orc_exact_knn_batch(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
                          int32_t k, int64_t* idx, double* dist, int32_t threads);
+void orc_exact_knn_batch_metric(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                                int32_t k, int32_t metric, int64_t* idx, double* dist, int32_t threads);
 
 int32_t orc_max_threads(void);
 
