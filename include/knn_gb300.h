@@ -57,6 +57,9 @@ typedef enum {
     KNN_STORE_FP8 = 2    /* FP8 e4m3, per-row scale s_i = max_j |x_ij| / 448 (1 for a zero row) */
 } knn_storage;
 
+/* Distance of the method: squared l2 (the paper's), or l1. */
+typedef enum { KNN_METRIC_L2SQ = 0, KNN_METRIC_L1 = 1 } knn_metric;
+
 /* Options of knn_adaptive. Fill with knn_opts_default() and change fields. */
 typedef struct {
     int32_t h;          /* extra set size: returned set has at most k+h points; -1 means h = k */
@@ -79,6 +82,11 @@ typedef struct {
                          * [0, span^2], so the bounds of Section 4 hold), the distance is exact
                          * once T + B_r >= M, and out_evals counts g per block drawn. With
                          * g x element size = 32 bytes a draw reads one DRAM sector. */
+    int32_t metric;     /* knn_metric: KNN_METRIC_L2SQ (default, the paper's squared l2) or KNN_METRIC_L1
+                         * (the l1 distance Section 3 names as a generalisation): samples |x_j - q_j|,
+                         * which lie in [0, span], so bounds are d^ -/+ span alpha(T); a stored copy
+                         * with element error e moves a sample by at most e (width (span + e) alpha + e);
+                         * the exact cap takes sum_j |x_j - q_j| on the FP32 data */
 } knn_opts;
 
 void knn_opts_default(knn_opts* opts);
@@ -228,7 +236,8 @@ knn_status knn_adaptive_ds_multi(const knn_dataset* ds, int32_t storage, const f
  * knn_rerank -- exact distances of candidate points, then top-k.
  *
  * For each query q, computes d = sum_j (X[c,j] - Q[q,j])^2 in FP64 for each
- * candidate c = cand[q, t] (t < ncand; entries < 0 are skipped) and returns
+ * candidate c = cand[q, t] (t < ncand; entries < 0 are skipped; the valid
+ * entries of a row must be distinct: a repeated index is ranked twice) and returns
  * the k smallest by (d, index) (Section 3's brute force restricted to the
  * candidates; the last step of returning the k nearest from the set S-hat).
  * out_idx: nq x k int64 (-1 padded when fewer valid candidates);
@@ -238,6 +247,12 @@ knn_status knn_adaptive_ds_multi(const knn_dataset* ds, int32_t storage, const f
 knn_status knn_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
                       const int64_t* cand, int32_t ncand, int32_t k,
                       int64_t* out_idx, double* out_dist, void* stream);
+
+/* knn_rerank under a distance (knn_metric): with KNN_METRIC_L1 the FP64
+ * distances are sum_j |X[c,j] - Q[q,j]| and out_dist holds them. */
+knn_status knn_rerank_metric(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                             const int64_t* cand, int32_t ncand, int32_t k, int32_t metric,
+                             int64_t* out_idx, double* out_dist, void* stream);
 
 /*
  * knn_exact -- the naive exact method (Section 3: all distances, then
@@ -251,6 +266,16 @@ size_t knn_exact_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k);
 knn_status knn_exact(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
                      int64_t* out_idx, double* out_dist,
                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* knn_exact under the l1 distance (the generalisation Section 3 names): FP32
+ * SIMT distances of every pair (each within a relative error (m+2) 2^-24 of
+ * the exact one; l1 has no product form for a tensor-core screen), every
+ * point within that margin of the k-th kept, FP64 l1 rerank. Same arguments,
+ * workspace (knn_exact_workspace_size) and outputs as knn_exact; out_dist
+ * holds l1 distances. */
+knn_status knn_exact_l1(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
+                        int64_t* out_idx, double* out_dist, void* workspace, size_t workspace_bytes,
+                        void* stream);
 
 /*
  * knn_exact_ds -- the naive exact method over a resident dataset, with a

@@ -23,6 +23,7 @@ extern "C" void knn_opts_default(knn_opts* o) {
   o->threads = 0;
   o->max_ctas = 0;
   o->block = 1;
+  o->metric = KNN_METRIC_L2SQ;
 }
 
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {

@@ -73,6 +73,7 @@ struct AdaptiveArgs {
   int32_t g;    // coordinates per sample (1: single coordinates; > 1: blocks of g consecutive ones)
   int32_t Mb;   // samples that make a distance exact: ceil(m / g)
   int32_t gvec; // a block is 32 bytes of the copy on 16-byte aligned rows: two 16-byte loads
+  int32_t l1;   // 1: l1 distance (samples |x - q|); 0: squared l2 (samples (x - q)^2)
   const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
   const float* R0min;   // smallest round-0 sum of each tile of points [nq][r0tiles] (null: no filter)
   int32_t r0tiles;      // tiles per query in R0min
@@ -186,6 +187,12 @@ __device__ __forceinline__ float alpha_of(const AdaptiveArgs& a, int64_t u) {
   return sqrtf(a.c_alpha * log1pf((1.0f + lu) * a.a_c1) / uu);
 }
 
+// One coordinate's term added to a partial sum: (x - q)^2 (squared l2, one
+// fused multiply-add) or |x - q| (l1).
+__device__ __forceinline__ float add_term(bool l1, float d, float part) {
+  return l1 ? part + fabsf(d) : fmaf(d, d, part);
+}
+
 // Value of rank `kth` (1-based) in the union of the ascending array A[0..na)
 // and the unordered array Bv[0..nb). Every thread gets the result.
 template <int NT>
@@ -254,7 +261,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
             const int64_t s = (int64_t)(8 * b) + w;
             if (s >= T && s < Tn) {
               const float d = (E::kScaled ? __fmul_rn(x[w], sc) : x[w]) - qs[s];
-              part = fmaf(d, d, part);
+              part = add_term(a.l1, d, part);
             }
           }
         }
@@ -333,7 +340,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
       for (int w = 0; w < 8; ++w) {
         if (ok[w]) {
           const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
-          part = fmaf(d, d, part);
+          part = add_term(a.l1, d, part);
         }
       }
     }
@@ -367,7 +374,8 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
 // words, elements in memory order) against the FP32 query values qb, added
 // to part in coordinate order.
 template <class E>
-__device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, const float* qb, float sc, float part) {
+__device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, const float* qb, float sc, float part,
+                                             bool l1) {
   constexpr int per = 4 / (int)sizeof(typename E::T);  // elements per 32-bit word
   const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
@@ -387,7 +395,7 @@ __device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, con
         x = E::conv((typename E::T)(word >> (8 * (c & 3))));
       if constexpr (E::kScaled) x = __fmul_rn(x, sc);
       const float d = x - qv[e];
-      part = fmaf(d, d, part);
+      part = add_term(l1, d, part);
     }
   }
   return part;
@@ -454,14 +462,14 @@ __device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qi
         for (int f = 0; f < F; ++f) {
           if (!ok[f]) continue;
           if (full[f]) {
-            part = block_sum32<E>(v[f][0], v[f][1], qs + cb[f], sc, part);
+            part = block_sum32<E>(v[f][0], v[f][1], qs + cb[f], sc, part, a.l1);
           } else {
             const int c1 = min(cb[f] + g, m);
             for (int c = cb[f]; c < c1; ++c) {
               float x = E::load(xr + c);
               if (E::kScaled) x = __fmul_rn(x, sc);
               const float d = x - qs[c];
-              part = fmaf(d, d, part);
+              part = add_term(a.l1, d, part);
             }
           }
         }
@@ -507,19 +515,19 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
         const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr + j));
         const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
         float d = x4.x - q4.x;
-        part = fmaf(d, d, part);
+        part = add_term(a.l1, d, part);
         d = x4.y - q4.y;
-        part = fmaf(d, d, part);
+        part = add_term(a.l1, d, part);
         d = x4.z - q4.z;
-        part = fmaf(d, d, part);
+        part = add_term(a.l1, d, part);
         d = x4.w - q4.w;
-        part = fmaf(d, d, part);
+        part = add_term(a.l1, d, part);
       }
     } else {
 #pragma unroll 4
       for (int j = lane; j < m; j += 32) {
         const float d = __ldg(xr + j) - qs[j];
-        part = fmaf(d, d, part);
+        part = add_term(a.l1, d, part);
       }
     }
 #pragma unroll
@@ -684,13 +692,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     // element error: the copy's samples lie in [0, (span + 2e)^2] and its
     // distances within eps of the data's, so the width of sampled bounds
     // grows by eps. Exact rounds read the FP32 data and keep width 0.
+    // (l1: a sample |x - q| lies in [0, span], normalised by span; a copy
+    // moves it by at most e, within [0, span + e])
     float spanw = span, eps = 0.0f;
     if (E::kStorage != KNN_STORE_F32) {
       const float e = *a.emax;
-      spanw = span + 2.0f * e;
-      eps = e * (2.0f * span + e);
+      spanw = a.l1 ? span + e : span + 2.0f * e;
+      eps = a.l1 ? e : e * (2.0f * span + e);
     }
-    const float span2 = spanw * spanw;
+    const float span2 = a.l1 ? spanw : spanw * spanw;
     if (bad || !isfinite(span2)) {
       for (int t = tid; t < stride; t += NT) oidx[t] = -1;
       if (tid == 0) {
@@ -991,7 +1001,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
             if (gl * 8 + w < a.B0) {
               const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
               const float d = xr[j] - __ldg(qr + j);
-              part = fmaf(d, d, part);
+              part = add_term(a.l1, d, part);
             }
           }
         } else {  // block samples, in gather_blocks' order
@@ -1001,7 +1011,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
               const int c1 = min(c0 + a.g, m);
               for (int c = c0; c < c1; ++c) {
                 const float d = xr[c] - __ldg(qr + c);
-                part = fmaf(d, d, part);
+                part = add_term(a.l1, d, part);
               }
             }
           }
@@ -1052,7 +1062,7 @@ static __global__ void permute_query_columns_kernel(const float* __restrict__ Q,
 // One point's round-0 sum against one staged query row v4 (the round loop's
 // order: blocks of 8 draws into partials, then the lane butterfly over G).
 template <int NB>
-__device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4, int nfull, int rem, int G) {
+__device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4, int nfull, int rem, int G, bool l1) {
   float p[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -1064,14 +1074,14 @@ __device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4,
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
           const float d = x[8 * b + w] - vv[w];
-          p[b] = fmaf(d, d, p[b]);
+          p[b] = add_term(l1, d, p[b]);
         }
       } else {
 #pragma unroll
         for (int w = 0; w < 8; ++w)
           if (w < rem) {
             const float d = x[8 * b + w] - vv[w];
-            p[b] = fmaf(d, d, p[b]);
+            p[b] = add_term(l1, d, p[b]);
           }
       }
     }
@@ -1122,6 +1132,7 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
   __syncthreads();
   if (((int64_t)blockIdx.x * kR0SharedThreads + (threadIdx.x & ~31)) >= n) return;  // warp-uniform
   const float4* v4 = reinterpret_cast<const float4*>(qv);
+  const bool l1 = a.l1;
   auto store = [&](int qq, float S) {
     const int qg = q0 + qq;
     if (i < n) R0[(size_t)qg * (size_t)n + i] = S;
@@ -1134,12 +1145,12 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
   };
   int qq = 0;
   for (; qq + 1 < qc; qq += 2) {  // two queries at a time: independent chains
-    const float S0 = r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G);
-    const float S1 = r0_shared_sum<NB>(x, v4 + (size_t)(qq + 1) * (W / 4), nfull, rem, G);
+    const float S0 = r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G, l1);
+    const float S1 = r0_shared_sum<NB>(x, v4 + (size_t)(qq + 1) * (W / 4), nfull, rem, G, l1);
     store(qq, S0);
     store(qq + 1, S1);
   }
-  if (qq < qc) store(qq, r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G));
+  if (qq < qc) store(qq, r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G, l1));
 }
 
 // Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and
@@ -1282,6 +1293,7 @@ static inline bool round0_applies(int32_t m, const knn_opts& o) { return o.B0 < 
 // 32-byte run of the copy on 16-byte aligned rows.
 template <class E>
 static inline void set_blocks(AdaptiveArgs& a, const knn_opts& o) {
+  a.l1 = o.metric == KNN_METRIC_L1 ? 1 : 0;  // (the metric rides along)
   const size_t elem = sizeof(typename E::T);
   const int32_t g = (E::kBlk && o.block > 1) ? o.block : 1;
   a.g = g;
@@ -1312,6 +1324,7 @@ static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double d
     return set_error("threads must be 0, 256, 512 or 1024"), KNN_EINVAL;
   if (o.grow != 0 && o.grow != 1) return set_error("grow must be 0 or 1"), KNN_EINVAL;
   if (o.block < 0 || o.block > 64) return set_error("block must be in [0, 64]"), KNN_EINVAL;
+  if (o.metric != KNN_METRIC_L2SQ && o.metric != KNN_METRIC_L1) return set_error("unknown metric"), KNN_EINVAL;
   return KNN_OK;
 }
 

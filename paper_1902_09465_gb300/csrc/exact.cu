@@ -17,7 +17,8 @@
 namespace knn {
 
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
-                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream);
+                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
+                         int32_t metric = KNN_METRIC_L2SQ);
 size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq);
 knn_status exact_tc(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k, int64_t* out_idx,
                     double* out_dist, void* workspace, size_t workspace_bytes, cudaStream_t stream);
@@ -47,11 +48,13 @@ __global__ void row_norms_kernel(const float* __restrict__ A, int64_t rows, int 
   if (lane == 0 && max_bits) atomicMax(max_bits, mx);
 }
 
-// FP32 SIMT screen: D[q*n + i] = xn[i] + qn[q] - 2 sum_j X[i,j] Q[q,j].
-// 128 x 128 tile (points x queries), k-step 8, 256 threads with 8 x 8
-// outputs each, double-buffered shared memory.
+// FP32 SIMT screen: D[q*n + i] = xn[i] + qn[q] - 2 sum_j X[i,j] Q[q,j]
+// (L1: D[q*n + i] = sum_j |X[i,j] - Q[q,j]|, each term and the sum in FP32,
+// in coordinate order). 128 x 128 tile (points x queries), k-step 8, 256
+// threads with 8 x 8 outputs each, double-buffered shared memory.
 constexpr int kBM = 128, kBN = 128, kBK = 8;
 
+template <bool L1>
 __global__ void __launch_bounds__(256) screen_sgemm_kernel(const float* __restrict__ X, const float* __restrict__ Q,
                                                            int64_t n, int nq, int m, const float* __restrict__ xn,
                                                            const float* __restrict__ qn, float* __restrict__ D) {
@@ -105,7 +108,12 @@ __global__ void __launch_bounds__(256) screen_sgemm_kernel(const float* __restri
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) {
+          if constexpr (L1)
+            acc[i][j] += fabsf(av[i] - bv[j]);
+          else
+            acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
     }
     if (more) {
 #pragma unroll
@@ -122,12 +130,15 @@ __global__ void __launch_bounds__(256) screen_sgemm_kernel(const float* __restri
   for (int j = 0; j < 8; ++j) {
     const int q = q0 + (j < 4 ? tq * 4 + j : 64 + tq * 4 + (j - 4));
     if (q >= nq) continue;
-    const float qv = qn[q];
     float* drow = D + (size_t)q * n;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int64_t p = p0 + (i < 4 ? tp * 4 + i : 64 + tp * 4 + (i - 4));
-      if (p < n) drow[p] = (xn[p] + qv) - 2.0f * acc[i][j];
+      if (p >= n) continue;
+      if constexpr (L1)
+        drow[p] = acc[i][j];
+      else
+        drow[p] = (xn[p] + qn[q]) - 2.0f * acc[i][j];
     }
   }
 }
@@ -165,14 +176,21 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(float* __restrict
   __syncthreads();
   select_smallest<kSelNT>([&](int i) { return f2key(__ldg(dr + i)); }, (int)n, k, hist, buf, ss, bs);
   const float tau = key2f(buf[k - 1]);
-  // FP32 arithmetic on non-negative terms: a few units of roundoff, covered
-  // by the factor 1.001 (the coefficients carry their own margins)
   const float u = 1.0f / 16777216.0f;
-  const float gm = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);
-  const float xmax = sqrtf(__uint_as_float(*xn_max_bits) * (1.0f + gm));
-  const float qq = sqrtf(qn[q] * (1.0f + gm));
-  const float E = 1.001f * (c_cross * xmax * qq + c_square * (xmax + qq) * (xmax + qq));
-  const float thr = (tau + 2.0f * E) * (1.0f + 4.0f * u);
+  float thr;
+  const bool relative = c_cross < 0.0f;  // screened values within a relative error -c_cross of the distances
+  if (relative) {
+    const float r = -c_cross;
+    thr = tau * ((1.0f + r) / (1.0f - r)) * (1.0f + 4.0f * u);
+  } else {
+    // FP32 arithmetic on non-negative terms: a few units of roundoff, covered
+    // by the factor 1.001 (the coefficients carry their own margins)
+    const float gm = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);
+    const float xmax = sqrtf(__uint_as_float(*xn_max_bits) * (1.0f + gm));
+    const float qq = sqrtf(qn[q] * (1.0f + gm));
+    const float E = 1.001f * (c_cross * xmax * qq + c_square * (xmax + qq) * (xmax + qq));
+    thr = (tau + 2.0f * E) * (1.0f + 4.0f * u);
+  }
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   int64_t* cr = cand + (size_t)q * kExactCand;
@@ -184,7 +202,7 @@ __global__ void __launch_bounds__(kSelNT) screen_select_kernel(float* __restrict
   }
   __syncthreads();
   int c = cnt;
-  if (c > kExactCand) {
+  if (c > kExactCand && !relative) {
     // second screen: direct FP32 distances of the window, one warp per point
     // (the screened row is scratch: window points get d32, the others +inf)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -316,7 +334,7 @@ extern "C" knn_status knn_exact(const float* X, int64_t n, int32_t m, const floa
     row_norms_kernel<<<di.sms * 8, 256, 0, stream>>>(X, n, m, c.xn, c.xmax);
     row_norms_kernel<<<(nq + 7) / 8, 256, 0, stream>>>(Q, nq, m, c.qn, nullptr);
     dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((nq + kBN - 1) / kBN));
-    screen_sgemm_kernel<<<grid, 256, 0, stream>>>(X, Q, n, nq, m, c.xn, c.qn, c.D);
+    screen_sgemm_kernel<false><<<grid, 256, 0, stream>>>(X, Q, n, nq, m, c.xn, c.qn, c.D);
     s = cuda_check(cudaGetLastError(), "exact kernels launch");
     if (s == KNN_OK)
       s = launch_screen_select(c.D, n, nq, m, k, c.qn, c.xmax, 0.0, simt_c_square(m), X, Q, c.cand, stream);
@@ -347,4 +365,43 @@ extern "C" knn_status knn_exact_ds(const knn_dataset* ds, int32_t screen, const 
   if (screen == KNN_SCREEN_BF16X3)
     return exact_tc(ds, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream);
   return knn_exact(ds->X, ds->n, ds->m, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream_);
+}
+
+// The naive exact method under the l1 distance: FP32 SIMT distances of every
+// pair (no product form exists for l1), each within a relative error
+// gamma_(m+2) of the exact distance; select within that margin; FP64 l1
+// rerank of the candidates.
+extern "C" knn_status knn_exact_l1(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, int32_t k,
+                                   int64_t* out_idx, double* out_dist, void* workspace, size_t workspace_bytes,
+                                   void* stream_) {
+  clear_error();
+  if (n < 1 || n >= (int64_t)1 << 31 || m < 1 || m > kMaxM || nq < 0 || k < 1 || k > n || k > kMaxKH) {
+    set_error("knn_exact_l1: need 1 <= n < 2^31, 1 <= m <= 16384, 1 <= k <= min(n, 1024)");
+    return KNN_EINVAL;
+  }
+  if (nq == 0) return KNN_OK;
+  if (!X || !Q || !out_idx || !out_dist) {
+    set_error("knn_exact_l1: null pointer");
+    return KNN_EINVAL;
+  }
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  Carve measure;
+  const size_t need = carve_exact(measure, n, nq, nullptr) + 256;
+  Workspace ws;
+  knn_status s = ws.acquire(workspace, workspace_bytes, need, stream);
+  if (s != KNN_OK) return s;
+  Carve cv;
+  cv.base = reinterpret_cast<uint8_t*>(((uintptr_t)ws.ptr + 255) & ~uintptr_t(255));
+  ExactCarve c;
+  carve_exact(cv, n, nq, &c);
+  const double u = 1.0 / 16777216.0;
+  const double rel = (double)(m + 2) * u / (1.0 - (double)(m + 2) * u);
+  dim3 grid((unsigned)((n + kBM - 1) / kBM), (unsigned)((nq + kBN - 1) / kBN));
+  screen_sgemm_kernel<true><<<grid, 256, 0, stream>>>(X, Q, n, nq, m, nullptr, nullptr, c.D);
+  s = cuda_check(cudaGetLastError(), "l1 screen launch");
+  if (s == KNN_OK)
+    s = launch_screen_select(c.D, n, nq, m, k, c.qn, c.xmax, -rel, 0.0, X, Q, c.cand, stream);
+  if (s == KNN_OK) s = launch_rerank(X, n, m, Q, nq, c.cand, kExactCand, k, out_idx, out_dist, stream, KNN_METRIC_L1);
+  ws.release();
+  return s;
 }

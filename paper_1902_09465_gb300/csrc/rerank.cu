@@ -40,11 +40,12 @@ __device__ void bitonic_sort_pairs(uint64_t* key, int64_t* idx, int P) {
   }
 }
 
-__device__ __forceinline__ double row_dist64(const float* xr, const float* qs, int m, int lane) {
+// Squared l2 distance (or l1 distance) of one row in FP64, one warp.
+__device__ __forceinline__ double row_dist64(const float* xr, const float* qs, int m, int lane, bool l1) {
   double s = 0.0;
   for (int j = lane; j < m; j += 32) {
     const double d = (double)__ldg(xr + j) - (double)qs[j];
-    s = fma(d, d, s);
+    s = l1 ? s + fabs(d) : fma(d, d, s);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -58,7 +59,8 @@ __device__ __forceinline__ double row_dist64(const float* xr, const float* qs, i
 template <int NT>
 __global__ void __launch_bounds__(NT) rerank_kernel(const float* __restrict__ X, int64_t n, int m,
                                                     const float* __restrict__ Q, const int64_t* __restrict__ cand,
-                                                    int ncand, int k, int64_t* out_idx, double* out_dist) {
+                                                    int ncand, int k, int64_t* out_idx, double* out_dist,
+                                                    int l1) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
   int64_t* idx = reinterpret_cast<int64_t*>(key + kRerankCap);
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(NT) rerank_kernel(const float* __restrict__ X,
     for (int t = warp; t < ncand; t += NT / 32) {
       const int64_t c = cr[t];
       if (c < 0 || c >= n) continue;
-      const double d = row_dist64(X + (size_t)c * m, qs, m, lane);
+      const double d = row_dist64(X + (size_t)c * m, qs, m, lane, l1 != 0);
       if (lane == 0) {
         key[t] = (uint64_t)__double_as_longlong(d);
         idx[t] = c;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(NT) rerank_kernel(const float* __restrict__ X,
       for (int t = warp; t < chunk; t += NT / 32) {
         const int64_t c = base + t;
         if (c >= n) break;
-        const double d = row_dist64(X + (size_t)c * m, qs, m, lane);
+        const double d = row_dist64(X + (size_t)c * m, qs, m, lane, l1 != 0);
         if (lane == 0) {
           key[k + t] = (uint64_t)__double_as_longlong(d);
           idx[k + t] = c;
@@ -123,13 +125,15 @@ __global__ void __launch_bounds__(NT) rerank_kernel(const float* __restrict__ X,
 }
 
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
-                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream) {
+                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
+                         int32_t metric) {
   const size_t smem = (size_t)kRerankCap * 16 + (size_t)m * 4;
   knn_status s = cuda_check(
       cudaFuncSetAttribute(rerank_kernel<kRerankNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
       "cudaFuncSetAttribute(rerank)");
   if (s != KNN_OK) return s;
-  rerank_kernel<kRerankNT><<<nq, kRerankNT, smem, stream>>>(X, n, m, Q, cand, ncand, k, out_idx, out_dist);
+  rerank_kernel<kRerankNT><<<nq, kRerankNT, smem, stream>>>(X, n, m, Q, cand, ncand, k, out_idx, out_dist,
+                                                            metric == KNN_METRIC_L1 ? 1 : 0);
   return cuda_check(cudaGetLastError(), "rerank_kernel launch");
 }
 
@@ -138,7 +142,17 @@ knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, i
 extern "C" knn_status knn_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
                                  const int64_t* cand, int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist,
                                  void* stream) {
+  return knn_rerank_metric(X, n, m, Q, nq, cand, ncand, k, KNN_METRIC_L2SQ, out_idx, out_dist, stream);
+}
+
+extern "C" knn_status knn_rerank_metric(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq,
+                                        const int64_t* cand, int32_t ncand, int32_t k, int32_t metric,
+                                        int64_t* out_idx, double* out_dist, void* stream) {
   knn::clear_error();
+  if (metric != KNN_METRIC_L2SQ && metric != KNN_METRIC_L1) {
+    knn::set_error("knn_rerank_metric: unknown metric");
+    return KNN_EINVAL;
+  }
   if (n < 1 || m < 1 || m > knn::kMaxM || nq < 0 || k < 1 || k > knn::kMaxKH || ncand < 1 ||
       ncand > knn::kRerankCap) {
     knn::set_error("knn_rerank: need n >= 1, 1 <= m <= 16384, 1 <= k <= 1024, 1 <= ncand <= 4096");
@@ -149,5 +163,6 @@ extern "C" knn_status knn_rerank(const float* X, int64_t n, int32_t m, const flo
     knn::set_error("knn_rerank: null pointer");
     return KNN_EINVAL;
   }
-  return knn::launch_rerank(X, n, m, Q, nq, cand, ncand, k, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+  return knn::launch_rerank(X, n, m, Q, nq, cand, ncand, k, out_idx, out_dist, static_cast<cudaStream_t>(stream),
+                            metric);
 }

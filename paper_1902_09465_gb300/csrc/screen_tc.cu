@@ -32,7 +32,8 @@
 namespace knn {
 
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
-                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream);
+                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
+                         int32_t metric = KNN_METRIC_L2SQ);
 knn_status launch_screen_select(float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
                                 const unsigned* xn_max_bits, double c_cross, double c_square, const float* X,
                                 const float* Q, int64_t* cand,

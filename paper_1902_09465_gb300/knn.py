@@ -35,7 +35,8 @@ class KnnError(RuntimeError):
 class Opts(C.Structure):
     _fields_ = [("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double), ("B0", C.c_int32),
                 ("B", C.c_int32), ("grow", C.c_int32), ("qid_base", C.c_uint64), ("mask_p", C.c_uint64),
-                ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32), ("block", C.c_int32)]
+                ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32), ("block", C.c_int32),
+                ("metric", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -45,6 +46,9 @@ _SIGS = {
     "knn_adaptive": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, C.c_double, C.c_uint64,
                                C.POINTER(Opts), _P, _P, _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "knn_rerank": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P]),
+    "knn_rerank_metric": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, _P, C.c_int32, C.c_int32, C.c_int32,
+                                    _P, _P, _P]),
+    "knn_exact_l1": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "knn_exact_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32, C.c_int32, C.c_int32]),
     "knn_exact": (C.c_int, [_P, C.c_int64, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "knn_dataset_create": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, _P, C.POINTER(C.c_void_p)]),
@@ -101,11 +105,14 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+METRICS = {"l2": 0, "l1": 1}
+
+
 def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid_base=0, share_points=False,
-              share_queries=False, max_ctas=0, threads=0, block=1) -> Opts:
+              share_queries=False, max_ctas=0, threads=0, block=1, metric="l2") -> Opts:
     """knn_opts for a call; `block` = coordinates per sample (1: single
     coordinates; g > 1: blocks of g consecutive coordinates, B0 and B then
-    count blocks)."""
+    count blocks); `metric` = "l2" (squared l2, the paper's) or "l1"."""
     o = Opts()
     lib().knn_opts_default(C.byref(o))
     o.h = -1 if h is None else int(h)
@@ -118,6 +125,7 @@ def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid
     o.max_ctas = int(max_ctas)
     o.threads = int(threads)
     o.block = int(block)
+    o.metric = METRICS[metric] if isinstance(metric, str) else int(metric)
     return o
 
 
@@ -284,15 +292,17 @@ class Dataset:
             pass
 
 
-def rerank(X: torch.Tensor, Q: torch.Tensor, cand: torch.Tensor, k: int, stream=None):
+def rerank(X: torch.Tensor, Q: torch.Tensor, cand: torch.Tensor, k: int, stream=None, metric="l2"):
     """Exact FP64 distances of the candidates of each query, top-k by
-    (distance, index) (knn_rerank). Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+    (distance, index) (knn_rerank_metric; squared l2 or l1 distances).
+    Returns (idx [nq,k] int64, dist [nq,k] f64)."""
     n, m = X.shape
     nq, ncand = cand.shape
     idx = torch.empty((nq, k), dtype=torch.int64, device=X.device)
     dist = torch.empty((nq, k), dtype=torch.float64, device=X.device)
-    rc = lib().knn_rerank(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, _dev(cand, "cand", torch.int64), ncand, int(k),
-                          _dev(idx, "idx", torch.int64), _dev(dist, "dist", torch.float64), _stream(stream))
+    rc = lib().knn_rerank_metric(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, _dev(cand, "cand", torch.int64), ncand,
+                                 int(k), METRICS[metric], _dev(idx, "idx", torch.int64),
+                                 _dev(dist, "dist", torch.float64), _stream(stream))
     _check(rc)
     return idx, dist
 
@@ -301,8 +311,10 @@ def exact_workspace_size(n, m, nq, k) -> int:
     return int(lib().knn_exact_workspace_size(int(n), int(m), int(nq), int(k)))
 
 
-def exact(X: torch.Tensor, Q: torch.Tensor, k: int, workspace: torch.Tensor | None = None, stream=None):
-    """Naive exact k-NN (knn_exact). Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+def exact(X: torch.Tensor, Q: torch.Tensor, k: int, workspace: torch.Tensor | None = None, stream=None,
+          metric="l2"):
+    """Naive exact k-NN (knn_exact; knn_exact_l1 with metric="l1").
+    Returns (idx [nq,k] int64, dist [nq,k] f64)."""
     n, m = X.shape
     nq = Q.shape[0]
     idx = torch.empty((nq, k), dtype=torch.int64, device=X.device)
@@ -310,8 +322,9 @@ def exact(X: torch.Tensor, Q: torch.Tensor, k: int, workspace: torch.Tensor | No
     ws_ptr, ws_bytes = None, 0
     if workspace is not None:
         ws_ptr, ws_bytes = _dev(workspace, "workspace", torch.uint8), workspace.numel()
-    rc = lib().knn_exact(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, int(k), _dev(idx, "idx", torch.int64),
-                         _dev(dist, "dist", torch.float64), ws_ptr, ws_bytes, _stream(stream))
+    fn = lib().knn_exact_l1 if metric == "l1" else lib().knn_exact
+    rc = fn(_dev(X, "X"), n, m, _dev(Q, "Q"), nq, int(k), _dev(idx, "idx", torch.int64),
+            _dev(dist, "dist", torch.float64), ws_ptr, ws_bytes, _stream(stream))
     _check(rc)
     return idx, dist
 

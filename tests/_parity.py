@@ -14,6 +14,7 @@ TOL_ESTIMATE = 1e-5   # FP32 sums vs FP64 sums on the same samples
 
 
 def run_gpu(X, Q, k, delta, seed, **opts):
+    """knn.adaptive with the decision log; numpy arrays out."""
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     Qd = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
     res = knn.adaptive(Xd, Qd, k, delta, seed, trace=True, **opts)
