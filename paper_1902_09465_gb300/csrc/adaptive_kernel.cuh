@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "knn_common.cuh"
 #include "knn_internal.h"
@@ -188,9 +189,14 @@ __device__ __forceinline__ float alpha_of(const AdaptiveArgs& a, int64_t u) {
 }
 
 // One coordinate's term added to a partial sum: (x - q)^2 (squared l2, one
-// fused multiply-add) or |x - q| (l1).
-__device__ __forceinline__ float add_term(bool l1, float d, float part) {
-  return l1 ? part + fabsf(d) : fmaf(d, d, part);
+// fused multiply-add) or |x - q| (l1). The metric is a template argument of
+// every gather; the round loop picks the instantiation once per call site.
+template <bool L1>
+__device__ __forceinline__ float add_term(float d, float part) {
+  if constexpr (L1)
+    return part + fabsf(d);
+  else
+    return fmaf(d, d, part);
 }
 
 // Value of rank `kth` (1-based) in the union of the ascending array A[0..na)
@@ -229,7 +235,7 @@ __device__ float kth_of_union(const float* A, int na, const float* Bv, int nb, i
 // power of two, at most 32); each lane walks its blocks of its points as one
 // flat sequence of items and computes the next item's Philox block while the
 // current item's 8 loads are in flight (software pipelining over items).
-template <int NT, class E>
+template <int NT, class E, bool L1>
 __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
                                                const float* qs, const int32_t* idc, float* Sc, float* Cc,
                                                uint32_t* hist) {
@@ -261,7 +267,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
             const int64_t s = (int64_t)(8 * b) + w;
             if (s >= T && s < Tn) {
               const float d = (E::kScaled ? __fmul_rn(x[w], sc) : x[w]) - qs[s];
-              part = add_term(a.l1, d, part);
+              part = add_term<L1>(d, part);
             }
           }
         }
@@ -340,7 +346,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
       for (int w = 0; w < 8; ++w) {
         if (ok[w]) {
           const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
-          part = add_term(a.l1, d, part);
+          part = add_term<L1>(d, part);
         }
       }
     }
@@ -373,9 +379,8 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
 // Sum of squared differences over one 32-byte block of the copy (two 16-byte
 // words, elements in memory order) against the FP32 query values qb, added
 // to part in coordinate order.
-template <class E>
-__device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, const float* qb, float sc, float part,
-                                             bool l1) {
+template <class E, bool L1>
+__device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, const float* qb, float sc, float part) {
   constexpr int per = 4 / (int)sizeof(typename E::T);  // elements per 32-bit word
   const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
@@ -395,7 +400,7 @@ __device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, con
         x = E::conv((typename E::T)(word >> (8 * (c & 3))));
       if constexpr (E::kScaled) x = __fmul_rn(x, sc);
       const float d = x - qv[e];
-      part = add_term(l1, d, part);
+      part = add_term<L1>(d, part);
     }
   }
   return part;
@@ -407,7 +412,7 @@ __device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, con
 // Philox block of 8 draws) and the reduction are those of gather_sampled. A
 // 32-byte block on 16-byte aligned rows (gvec) is two 16-byte loads, F draws
 // in flight per lane; a ragged last block is read element by element.
-template <int NT, class E>
+template <int NT, class E, bool L1>
 __device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
                                               const float* qs, const int32_t* idc, float* Sc, float* Cc,
                                               uint32_t* hist) {
@@ -462,14 +467,14 @@ __device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qi
         for (int f = 0; f < F; ++f) {
           if (!ok[f]) continue;
           if (full[f]) {
-            part = block_sum32<E>(v[f][0], v[f][1], qs + cb[f], sc, part, a.l1);
+            part = block_sum32<E, L1>(v[f][0], v[f][1], qs + cb[f], sc, part);
           } else {
             const int c1 = min(cb[f] + g, m);
             for (int c = cb[f]; c < c1; ++c) {
               float x = E::load(xr + c);
               if (E::kScaled) x = __fmul_rn(x, sc);
               const float d = x - qs[c];
-              part = add_term(a.l1, d, part);
+              part = add_term<L1>(d, part);
             }
           }
         }
@@ -500,7 +505,7 @@ __device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qi
 
 // Exact round: one warp per active point, the full FP32 row of the data
 // (16-byte loads when rows are 16-byte aligned).
-template <int NT>
+template <int NT, bool L1>
 __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int nact, const float* qs,
                                              const int32_t* idc, float* Sc, uint32_t* hist) {
   const int m = a.m;
@@ -515,19 +520,19 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
         const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr + j));
         const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
         float d = x4.x - q4.x;
-        part = add_term(a.l1, d, part);
+        part = add_term<L1>(d, part);
         d = x4.y - q4.y;
-        part = add_term(a.l1, d, part);
+        part = add_term<L1>(d, part);
         d = x4.z - q4.z;
-        part = add_term(a.l1, d, part);
+        part = add_term<L1>(d, part);
         d = x4.w - q4.w;
-        part = add_term(a.l1, d, part);
+        part = add_term<L1>(d, part);
       }
     } else {
 #pragma unroll 4
       for (int j = lane; j < m; j += 32) {
         const float d = __ldg(xr + j) - qs[j];
-        part = add_term(a.l1, d, part);
+        part = add_term<L1>(d, part);
       }
     }
 #pragma unroll
@@ -624,7 +629,7 @@ __device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, flo
   return total;
 }
 
-template <int NT, class E>
+template <int NT, class E, bool L1>
 __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(AdaptiveArgs a) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   __shared__ AdaptiveShared<NT> sh;
@@ -749,13 +754,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         nact = round0_filter<NT>(a, q, n, k, w, Tf, hist, buf, sh, ids0 + (size_t)cur * n, Sc,
                                  ids0 + (size_t)(cur ^ 1) * n, S0 + (size_t)(cur ^ 1) * n, lcode, lS, &min_elim);
       else if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
-        gather_exact<NT>(a, r, nact, qs, idc, Sc, hist);
+        gather_exact<NT, L1>(a, r, nact, qs, idc, Sc, hist);
       else if (pre)
         for (int i = tid; i < nact; i += NT) atomicAdd(&hist[f2key(Sc[i]) >> 20], 1u);
       else if constexpr (E::kBlk)
-        gather_blocks<NT, E>(a, qid, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
+        gather_blocks<NT, E, L1>(a, qid, r, nact, T, Tn, qs, idc, Sc, Cc, hist);
       else
-        gather_sampled<NT, E>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
+        gather_sampled<NT, E, L1>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
       const bool ident = (r == 0) && !flt;  // slot s holds point s
 
@@ -960,7 +965,7 @@ static inline int round0_rows(int m) {
   return r < 1 ? 1 : (r > kR0MaxRows ? kR0MaxRows : r);
 }
 
-template <class E>
+template <class E, bool L1>
 __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int rows_per_cta, float* R0,
                                                             float* R0min) {
   extern __shared__ __align__(16) float rows[];
@@ -1001,7 +1006,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
             if (gl * 8 + w < a.B0) {
               const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
               const float d = xr[j] - __ldg(qr + j);
-              part = add_term(a.l1, d, part);
+              part = add_term<L1>(d, part);
             }
           }
         } else {  // block samples, in gather_blocks' order
@@ -1011,7 +1016,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
               const int c1 = min(c0 + a.g, m);
               for (int c = c0; c < c1; ++c) {
                 const float d = xr[c] - __ldg(qr + c);
-                part = add_term(a.l1, d, part);
+                part = add_term<L1>(d, part);
               }
             }
           }
@@ -1061,8 +1066,8 @@ static __global__ void permute_query_columns_kernel(const float* __restrict__ Q,
 
 // One point's round-0 sum against one staged query row v4 (the round loop's
 // order: blocks of 8 draws into partials, then the lane butterfly over G).
-template <int NB>
-__device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4, int nfull, int rem, int G, bool l1) {
+template <int NB, bool L1>
+__device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4, int nfull, int rem, int G) {
   float p[NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -1074,14 +1079,14 @@ __device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4,
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
           const float d = x[8 * b + w] - vv[w];
-          p[b] = add_term(l1, d, p[b]);
+          p[b] = add_term<L1>(d, p[b]);
         }
       } else {
 #pragma unroll
         for (int w = 0; w < 8; ++w)
           if (w < rem) {
             const float d = x[8 * b + w] - vv[w];
-            p[b] = add_term(l1, d, p[b]);
+            p[b] = add_term<L1>(d, p[b]);
           }
       }
     }
@@ -1095,7 +1100,7 @@ __device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4,
   return p[0];
 }
 
-template <class E, int NB>
+template <class E, int NB, bool L1>
 __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, const float* Qp, float* R0,
                                                                          float* R0min) {
   // grid: x = tiles of kR0SharedThreads points, y = slices of kQ queries
@@ -1132,7 +1137,6 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
   __syncthreads();
   if (((int64_t)blockIdx.x * kR0SharedThreads + (threadIdx.x & ~31)) >= n) return;  // warp-uniform
   const float4* v4 = reinterpret_cast<const float4*>(qv);
-  const bool l1 = a.l1;
   auto store = [&](int qq, float S) {
     const int qg = q0 + qq;
     if (i < n) R0[(size_t)qg * (size_t)n + i] = S;
@@ -1145,12 +1149,12 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
   };
   int qq = 0;
   for (; qq + 1 < qc; qq += 2) {  // two queries at a time: independent chains
-    const float S0 = r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G, l1);
-    const float S1 = r0_shared_sum<NB>(x, v4 + (size_t)(qq + 1) * (W / 4), nfull, rem, G, l1);
+    const float S0 = r0_shared_sum<NB, L1>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G);
+    const float S1 = r0_shared_sum<NB, L1>(x, v4 + (size_t)(qq + 1) * (W / 4), nfull, rem, G);
     store(qq, S0);
     store(qq + 1, S1);
   }
-  if (qq < qc) store(qq, r0_shared_sum<NB>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G, l1));
+  if (qq < qc) store(qq, r0_shared_sum<NB, L1>(x, v4 + (size_t)qq * (W / 4), nfull, rem, G));
 }
 
 // Range of the finite data as ordered keys, xr[0] = min, xr[1] = max, and
@@ -1200,12 +1204,17 @@ struct AdaptivePlan {
 };
 
 // The round-loop kernel instantiated for a thread count (256, 512 or 1024;
-// all keep 64 registers per thread: 8, 16 or 32 warps per query).
+// all keep 64 registers per thread: 8, 16 or 32 warps per query) and a metric.
+template <class E, bool L1>
+static void* rounds_kernel_for_metric(int threads) {
+  if (threads == 256) return reinterpret_cast<void*>(adaptive_rounds_kernel<256, E, L1>);
+  if (threads == 1024) return reinterpret_cast<void*>(adaptive_rounds_kernel<1024, E, L1>);
+  return reinterpret_cast<void*>(adaptive_rounds_kernel<512, E, L1>);
+}
+
 template <class E>
-static void* rounds_kernel_for(int threads) {
-  if (threads == 256) return reinterpret_cast<void*>(adaptive_rounds_kernel<256, E>);
-  if (threads == 1024) return reinterpret_cast<void*>(adaptive_rounds_kernel<1024, E>);
-  return reinterpret_cast<void*>(adaptive_rounds_kernel<512, E>);
+static void* rounds_kernel_for(int threads, bool l1) {
+  return l1 ? rounds_kernel_for_metric<E, true>(threads) : rounds_kernel_for_metric<E, false>(threads);
 }
 
 template <class E>
@@ -1215,7 +1224,7 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   if (s != KNN_OK) return s;
   p->threads = (o && (o->threads == 256 || o->threads == 1024)) ? o->threads : kAdaptiveNT;
   p->smem = adaptive_smem_bytes(m, E::kPerm);
-  const void* fn = rounds_kernel_for<E>(p->threads);
+  const void* fn = rounds_kernel_for<E>(p->threads, o && o->metric == KNN_METRIC_L1);
   s = cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
                  "cudaFuncSetAttribute(adaptive)");
   if (s != KNN_OK) return s;
@@ -1237,14 +1246,22 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   return KNN_OK;
 }
 
+template <class E, bool L1>
+static void launch_rounds_metric(const AdaptivePlan& p, const AdaptiveArgs& a, cudaStream_t stream) {
+  if (p.threads == 256)
+    adaptive_rounds_kernel<256, E, L1><<<p.grid, 256, p.smem, stream>>>(a);
+  else if (p.threads == 1024)
+    adaptive_rounds_kernel<1024, E, L1><<<p.grid, 1024, p.smem, stream>>>(a);
+  else
+    adaptive_rounds_kernel<512, E, L1><<<p.grid, 512, p.smem, stream>>>(a);
+}
+
 template <class E>
 static knn_status launch_rounds(const AdaptivePlan& p, const AdaptiveArgs& a, cudaStream_t stream) {
-  if (p.threads == 256)
-    adaptive_rounds_kernel<256, E><<<p.grid, 256, p.smem, stream>>>(a);
-  else if (p.threads == 1024)
-    adaptive_rounds_kernel<1024, E><<<p.grid, 1024, p.smem, stream>>>(a);
+  if (a.l1)
+    launch_rounds_metric<E, true>(p, a, stream);
   else
-    adaptive_rounds_kernel<512, E><<<p.grid, 512, p.smem, stream>>>(a);
+    launch_rounds_metric<E, false>(p, a, stream);
   return cuda_check(cudaGetLastError(), "adaptive_rounds_kernel launch");
 }
 

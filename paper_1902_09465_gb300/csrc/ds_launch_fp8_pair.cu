@@ -1,0 +1,8 @@
+// ds_launch_fp8_pair.cu -- the dataset launch gathering from the FP8 copy
+// with per-pair draws; see dataset_launch.cuh (one element type per translation
+// unit, so the kernels compile in parallel).
+#include "dataset_launch.cuh"
+
+namespace knn {
+template KNN_DS_LAUNCH_DECL(ElemFP8);
+}  // namespace knn
