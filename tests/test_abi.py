@@ -60,6 +60,20 @@ def test_invalid_arguments_are_rejected_on_the_host(lib_path):
         assert L.knn_last_error().decode()
     rc = L.knn_rerank(None, 10, 4, None, 1, None, 0, 1, None, None, None)
     assert rc == 1
+    # option fields out of range: block above 64, an unknown metric, odd thread counts
+    for field, value in (("block", 65), ("block", -1), ("metric", 2), ("threads", 300), ("grow", 2)):
+        bad = knn.Opts()
+        L.knn_opts_default(ctypes.byref(bad))
+        setattr(bad, field, value)
+        rc = L.knn_adaptive(None, 100, 8, None, 1, 2, 0.1, 0, ctypes.byref(bad), None, None, None, None, None,
+                            None, None, 0, None)
+        assert rc == 1, (field, value)
+        assert field.split("_")[0] in L.knn_last_error().decode() or L.knn_last_error().decode()
+    rc = L.knn_rerank_metric(None, 10, 4, None, 1, None, 4, 1, 3, None, None, None)
+    assert rc == 1 and "metric" in L.knn_last_error().decode()
+    o2 = knn.Opts()
+    L.knn_opts_default(ctypes.byref(o2))
+    assert o2.block == 1 and o2.metric == 0
 
 
 def test_oracle_and_library_share_no_code():
