@@ -62,3 +62,17 @@ def test_filtered_round0_replays_in_the_oracle():
     gpu = {key: v.cpu().numpy() for key, v in g.items()}
     summ, _ = check(X, Q, 5, delta=0.01, seed=2, bound="exp", c_alpha=1e-4, B0=8, B=8, grow=1, gpu=gpu)
     assert summ["queries"] == 6
+
+
+@pytest.mark.parametrize("n,k", [(320, 10), (321, 10), (352, 11), (2048, 64)])
+def test_filter_with_as_many_tiles_as_k(n, k):
+    """Tiles of 32 rows: n = 320 gives exactly k = 10 tile minima (the k-th
+    smallest is the largest of them), 321 one more, 352 with k = 11 again
+    exactly k; the rounds must equal the unfiltered path."""
+    X, Q, _ = synth.gaussian_planted(n, 64, 2, nq=3, seed=n)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    opt = dict(bound="exp", c_alpha=1e-4, B0=8, B=8, grow=1, h=min(k, n - k))
+    with knn.Dataset(Xd, copies=()) as ds:
+        a = ds.adaptive(Qd, k, 0.01, 6, trace=True, **opt)
+    b = knn.adaptive(Xd, Qd, k, 0.01, 6, trace=True, **opt)
+    _same(a, b)
