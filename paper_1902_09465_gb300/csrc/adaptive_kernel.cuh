@@ -75,6 +75,7 @@ struct AdaptiveArgs {
   int32_t Mb;   // samples that make a distance exact: ceil(m / g)
   int32_t gvec; // a block is 32 bytes of the copy on 16-byte aligned rows: two 16-byte loads
   int32_t l1;   // 1: l1 distance (samples |x - q|); 0: squared l2 (samples (x - q)^2)
+  int32_t qvec; // query rows start on 16-byte boundaries (m % 4 == 0 and Q aligned): 16-byte loads
   const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
   const float* R0min;   // smallest round-0 sum of each tile of points [nq][r0tiles] (null: no filter)
   int32_t r0tiles;      // tiles per query in R0min
@@ -1010,13 +1011,25 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
             }
           }
         } else {  // block samples, in gather_blocks' order
+          const bool vec4 = a.qvec && (a.g & 3) == 0;  // staged rows and query rows 16-byte aligned
           for (int w = 0; w < 8; ++w) {
             if (gl * 8 + w < a.B0) {
               const int c0 = (int)__umulhi(philox_word(ph, w), (uint32_t)a.Mb) * a.g;
               const int c1 = min(c0 + a.g, m);
-              for (int c = c0; c < c1; ++c) {
-                const float d = xr[c] - __ldg(qr + c);
-                part = add_term<L1>(d, part);
+              if (vec4 && c1 - c0 == a.g) {
+                for (int c = c0; c < c1; c += 4) {
+                  const float4 x4 = *reinterpret_cast<const float4*>(xr + c);
+                  const float4 q4 = __ldg(reinterpret_cast<const float4*>(qr + c));
+                  part = add_term<L1>(x4.x - q4.x, part);
+                  part = add_term<L1>(x4.y - q4.y, part);
+                  part = add_term<L1>(x4.z - q4.z, part);
+                  part = add_term<L1>(x4.w - q4.w, part);
+                }
+              } else {
+                for (int c = c0; c < c1; ++c) {
+                  const float d = xr[c] - __ldg(qr + c);
+                  part = add_term<L1>(d, part);
+                }
               }
             }
           }
@@ -1310,7 +1323,8 @@ static inline bool round0_applies(int32_t m, const knn_opts& o) { return o.B0 < 
 // 32-byte run of the copy on 16-byte aligned rows.
 template <class E>
 static inline void set_blocks(AdaptiveArgs& a, const knn_opts& o) {
-  a.l1 = o.metric == KNN_METRIC_L1 ? 1 : 0;  // (the metric rides along)
+  a.l1 = o.metric == KNN_METRIC_L1 ? 1 : 0;  // (the metric and the query alignment ride along)
+  a.qvec = (a.m % 4 == 0 && ((uintptr_t)a.Q & 15) == 0) ? 1 : 0;
   const size_t elem = sizeof(typename E::T);
   const int32_t g = (E::kBlk && o.block > 1) ? o.block : 1;
   a.g = g;
