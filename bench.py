@@ -439,6 +439,8 @@ def run_ours(args, rank, world, local_rank):
                                                "ms_per_batch": round(exact_simt_ms, 4)}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 5), "traffic": traffic,
+                     "dram_gbs": round(traffic / (kern_ms / 1e3) / 1e9, 2) if traffic else None,
+                     "dram_frac": round(traffic / (kern_ms / 1e3) / 1e9 / hbm, 5) if traffic else None,
                      "kernel": f"knn_adaptive_ds call = round0_kernel<ElemF32> + adaptive_rounds_kernel<{best['threads']}, "
                                "ElemF32>",
                      "kernel_ms": round(kern_ms, 4),
@@ -446,7 +448,8 @@ def run_ours(args, rank, world, local_rank):
                      "sector_gbs": round(sector_gbs, 2),
                      "note": "algorithmic bytes: X once + round-0 sums written and read + 4 B per coordinate "
                              "evaluation after round 0 + query rows; sector_gbs counts 32 B per evaluation (the DRAM "
-                             "granule a random 4-byte gather moves)"},
+                             "granule a random 4-byte gather moves); dram_gbs = the captured DRAM traffic of one "
+                             "call over the live call time (round-0 pass + round loop)"},
         "e2e": {"value": round(world * nq / (e2e_ms / 1e3), 3), "unit": "queries/s",
                 "h2d_bytes_per_step": nq * m * 4, "d2h_bytes_per_step": nq * k * 16},
         "gpu_launches": launches_per_step * args.steps,
