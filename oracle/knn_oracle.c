@@ -313,7 +313,8 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
      * the width of the sampled bounds grows accordingly. The exact cap reads
      * the FP32 data, so exact distances keep width 0.
      * For l1 a sample |x - q| lies in [0, span] (normalised by span, not
-     * span^2), and a copy moves it by at most emax, within [0, span + emax]. */
+     * span^2), and a copy moves it by at most emax, within [0, span + emax].
+     * (eps is the round-0 copy term; later rounds may use a smaller one.) */
     const int32_t metric = p->metric;
     const double spanw = metric == ORC_METRIC_L1 ? span + emax : span + 2.0 * emax;
     const double span2 = metric == ORC_METRIC_L1 ? spanw : spanw * spanw;
@@ -360,9 +361,23 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
             Tx[i] = (int32_t)Tn;
         }
         evals += nact * (exact ? (int64_t)m : Br * g);
-        const double w = exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta) + eps;
         /* estimate: mean per coordinate of the sampled blocks (S / (T g)) */
         const double Tg = (double)Tn * (double)g;
+        /* A copy's sample differs from the data's by at most e (2 |xt - q| + e),
+         * so its mean over the sampled coordinates by at most e (2 mean|xt - q|
+         * + e) <= e (2 sqrt(d_i) + e), d_i the copy's estimate (the mean of
+         * |z| is at most the square root of the mean of z^2). After round 0
+         * the width takes the largest estimate among the points it decides,
+         * when that is below the span form. */
+        double eps_r = eps;
+        if (!exact && r > 0 && emax > 0.0 && metric != ORC_METRIC_L1) {
+            double dmax = 0.0;
+            for (int64_t i = 0; i < n; ++i)
+                if (status[i] == ORC_ACTIVE && Sx[i] / Tg > dmax) dmax = Sx[i] / Tg;
+            const double e2 = emax * (2.0 * sqrt(dmax) + emax);
+            if (e2 < eps_r) eps_r = e2;
+        }
+        const double w = exact ? 0.0 : span2 * orc_alpha(p->bound, p->c_alpha, Tn, n, p->delta) + eps_r;
 
         /* Bounds of the non-eliminated points: current ones for active
          * points, frozen ones for accepted points. */

@@ -363,3 +363,40 @@ def test_stored_copies_keep_the_guarantee():
         for q in range(4):
             c = r["stats"][q]["count"]
             assert c <= 8 and set(ti[q]) <= set(r["idx"][q][:c])
+
+
+@pytest.mark.parametrize("target,decided", [("between_new_and_old", True), ("below_half_factor", False)])
+def test_copy_width_after_round_0_uses_the_active_estimates(target, decided):
+    """Closed-form case for the copy term of the width. Query and point 0 at
+    0, points 1 and 2 at 257 (their BF16 copy holds 256: error e = 1), point 3
+    at 4096 (exact; it fixes span = 4096 and leaves in round 0). In round 1 the
+    active points' largest copy estimate is 256^2, so the copy term is
+    e (2 * 256 + e) = 513 instead of the span form e (2 * 4096 + e) = 8193.
+    Points 1 and 2 (estimate 65536) are eliminated and point 0 accepted in
+    round 1 iff the width w1 = span'^2 alpha(4) + 513 is below 32768: alpha(4)
+    is set so that this holds, but would fail with the span form (case 1), or
+    so that it fails, but would hold with half the copy term (case 2)."""
+    n, m, delta, e, span = 4, 32, 0.01, 1.0, 4096.0
+    X = np.zeros((n, m), dtype=np.float32)
+    X[1:3] = 257.0
+    X[3] = 4096.0
+    q = np.zeros((1, m), dtype=np.float32)
+    _, _, emax = oracle.quantize(X, "bf16")
+    assert emax == e
+    sp2 = (span + 2 * e) ** 2
+    lg = lambda u: math.log(1.0 + (1.0 + math.log(u)) * n / delta)
+    if target == "between_new_and_old":
+        a4 = (32768 - 0.5 * (513 + 8193)) / sp2          # w1 < 32768 with 513, > with 8193
+    else:
+        a4 = (32768 - 0.5 * (513 + 257)) / sp2           # w1 > 32768 with 513, < with 257
+    c = a4 * a4 * 4 / lg(4)
+    a2 = math.sqrt(c * lg(2) / 2)
+    assert sp2 * a2 + e * (2 * span + e) > 32768         # round 0 decides points 0-2 neither way
+    r = oracle.adaptive(X, q, oracle.make_params(1, h=0, delta=delta, bound="exp", c_alpha=c, B0=2, B=2,
+                                                 storage="bf16"))
+    rounds = r["code"][0] >> 2
+    assert rounds[3] == 0 and (r["code"][0][3] & 3) == oracle.ELIMINATED
+    if decided:
+        assert r["stats"][0]["rounds"] == 2 and list(r["idx"][0]) == [0]
+    else:
+        assert np.all(rounds[:3] >= 2)
