@@ -700,9 +700,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     // grows by eps. Exact rounds read the FP32 data and keep width 0.
     // (l1: a sample |x - q| lies in [0, span], normalised by span; a copy
     // moves it by at most e, within [0, span + e])
-    float spanw = span, eps = 0.0f;
+    float spanw = span, eps = 0.0f, ecopy = 0.0f;
     if (E::kStorage != KNN_STORE_F32) {
       const float e = *a.emax;
+      ecopy = e;
       spanw = a.l1 ? span + e : span + 2.0f * e;
       eps = a.l1 ? e : e * (2.0f * span + e);
     }
@@ -747,7 +748,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       float* Sc = pre && !flt ? const_cast<float*>(a.R0) + (size_t)q * (size_t)n : S0 + (size_t)cur * n;
       float* Cc = C0 + (size_t)cur * n;
       evals += (int64_t)nact * (exact ? (int64_t)m : Br * a.g);
-      const float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
+      float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
       const float Tf = (float)(Tn * a.g);  // estimate = S / (T g): mean per coordinate
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
@@ -764,6 +765,17 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         gather_sampled<NT, E, L1>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
       const bool ident = (r == 0) && !flt;  // slot s holds point s
+      // After round 0 a copy's term shrinks to e (2 sqrt(d_max) + e), d_max the
+      // largest estimate among the points decided now: a copy moves a sample by
+      // at most e (2 |x~ - q| + e), and the mean of |x~ - q| is at most the square
+      // root of the mean of (x~ - q)^2.
+      if (!L1 && E::kStorage != KNN_STORE_F32 && r > 0 && !exact && ecopy > 0.0f) {
+        float mx = 0.0f;
+        for (int i = tid; i < nact; i += NT) mx = fmaxf(mx, Sc[i]);
+        mx = block_max<NT>(mx, sh.bs);
+        const float e2 = ecopy * (2.0f * sqrtf(mx / Tf) + ecopy);
+        if (e2 < eps) w = span2 * alpha_of(a, Tn) + e2;
+      }
 
       // ---- thresholds
       const int kk = min(k + 1, nact);
