@@ -327,9 +327,9 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- shared coordinates (both counter masks zero): column-permuted copies, contiguous row prefixes
     shared = {}
-    ds.share(0, copies=("f32", "bf16"))
+    ds.share(0, copies=("f32", "bf16", "fp8"))
     SH = dict(share_points=True, share_queries=True)
-    for storage in ("f32", "bf16"):
+    for storage in ("f32", "bf16", "fp8"):
         t = runtime.autotune(ds, Hd, k, w["delta"], storage=storage, target=RECALL_TARGET, margin=0.0005,
                              c_grid=[args.c_alpha] if args.c_alpha else C_GRID, use_cache=False, extra=SH,
                              cache=os.path.join(tempfile.gettempdir(), f"knn_bench_tune_sh_{os.getpid()}.json"))
@@ -349,7 +349,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms_s = max_over_ranks(v0.elapsed_time(v1) / vsteps)
         ev_s = int(res_s["evals"].sum().item())
-        elem = 4 if storage == "f32" else 2
+        elem = {"f32": 4, "bf16": 2, "fp8": 1}[storage]
         shared[storage] = {
             "queries_per_s": round(world * nq / (ms_s / 1e3), 3), "ms_per_step": round(ms_s, 4),
             "recall": round(recall_of(ri_s.cpu().numpy(), rd_s.cpu().numpy(), ti_np, td_np), 6),
@@ -358,7 +358,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- block samples (a draw reads one 32-byte block: 8 FP32 / 16 BF16 coordinates)
     blocks = {}
-    for storage, g in (("f32", 8), ("bf16", 16)):
+    for storage, g in (("f32", 8), ("bf16", 16), ("fp8", 32)):
         t = runtime.autotune(ds, Hd, k, w["delta"], storage=storage, target=RECALL_TARGET, margin=0.0005,
                              schedules=((2, 2, 1), (4, 4, 1), (8, 8, 1)), use_cache=False, extra={"block": g},
                              c_grid=[args.c_alpha] if args.c_alpha else C_GRID + [1e-5, 3e-6],
@@ -379,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms_s = max_over_ranks(v0.elapsed_time(v1) / vsteps)
         ev_s = int(res_s["evals"].sum().item())
-        elem = 4 if storage == "f32" else 2
+        elem = {"f32": 4, "bf16": 2, "fp8": 1}[storage]
         blocks[f"{storage}_g{g}"] = {
             "queries_per_s": round(world * nq / (ms_s / 1e3), 3), "ms_per_step": round(ms_s, 4),
             "recall": round(recall_of(ri_s.cpu().numpy(), rd_s.cpu().numpy(), ti_np, td_np), 6),
