@@ -138,6 +138,18 @@ def make_inputs(rank: int, world: int = 1):
     return X, Q, H
 
 
+def reduce_max(v: float, world: int, device) -> float:
+    """Largest v over the ranks (one all-reduce of a scalar: the replicas'
+    step time is the slowest rank's). NCCL on CUDA tensors, gloo on CPU ones."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def recall_of(got_idx, got_d, true_idx, true_d, rel=1e-6):
     """Fraction of the true k nearest returned; a returned point whose exact
     distance ties the k-th true distance within `rel` also counts."""
@@ -208,11 +220,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, dev)
 
     # ---- timed region: K full steps
     clocks = ClockSampler(local_rank)
