@@ -78,6 +78,7 @@ def recall(got_idx, got_dist, true_idx, true_dist, rel: float = 1e-6) -> float:
 
 
 DEFAULT_SCHEDULES = ((16, 16, 1), (8, 8, 1), (32, 32, 1), (16, 16, 0), (32, 16, 0))
+BLOCK_SCHEDULES = ((2, 2, 1), (4, 4, 1), (8, 8, 1))  # in blocks of coordinates
 DEFAULT_C_GRID = (1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5)
 
 
@@ -95,17 +96,22 @@ def tune_key(ds: knn.Dataset, k: int, storage: str) -> str:
 def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, storage: str = "f32",
              target: float = 0.999, margin: float = 0.0005, schedules=DEFAULT_SCHEDULES, threads=(512, 1024),
              c_grid=DEFAULT_C_GRID, reps: int = 3, cache: str | None = None, use_cache: bool = True,
-             seed: int = 0, extra=None):
-    """Picks (B0, B, grow, threads, C_alpha) for a dataset: for every
-    schedule and thread count, the smallest C_alpha of the grid whose recall
-    on the held-out queries H (after the FP64 rerank) is at least
-    target + margin, then the fastest of those. Returns a dict with the
-    choice and the whole table, and stores it in the JSON cache under a key of
-    (d, n bucket, storage, k). `extra` adds options to every call (for
-    example the shared-coordinate masks); `seed` is the Philox seed used."""
+             seed: int = 0, extra=None, blocks=(1,), block_schedules=BLOCK_SCHEDULES):
+    """Picks (block, B0, B, grow, threads, C_alpha) for a dataset: for every
+    sampling unit in `blocks` (1: single coordinates, g > 1: blocks of g
+    coordinates, tried with `block_schedules`), schedule and thread count,
+    the smallest C_alpha of the grid whose recall on the held-out queries H
+    (after the FP64 rerank) is at least target + margin, then the fastest of
+    those. Returns a dict with the choice and the whole table, and stores it
+    in the JSON cache under a key of (d, n bucket, storage, k, options).
+    `extra` adds options to every call (for example the shared-coordinate
+    masks); `seed` is the Philox seed used."""
     path = _cache_path(cache)
     extra = dict(extra or {})
+    blocks = tuple(int(g) for g in blocks)
     key = tune_key(ds, k, storage) + ("|" + ",".join(f"{a}={b}" for a, b in sorted(extra.items())) if extra else "")
+    if blocks != (1,):
+        key += "|blocks=" + ",".join(str(g) for g in blocks)
     if use_cache and os.path.exists(path):
         try:
             with open(path) as f:
@@ -116,9 +122,12 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
             pass
     ti, td = ds.exact(H, k, screen="f32")
     table = []
-    for (B0, B, grow) in schedules:
+    plan = [(g, sch) for g in blocks for sch in (schedules if g <= 1 else block_schedules)]
+    for g, (B0, B, grow) in plan:
         for th in threads:
             opts = dict(bound="exp", B0=B0, B=B, grow=grow, threads=th, qid_base=1 << 41, **extra)
+            if g > 1:
+                opts["block"] = g
             chosen = None
             for c in c_grid:
                 res = ds.adaptive(H, k, delta, seed, storage=storage, c_alpha=c, **opts)
@@ -138,8 +147,10 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
                 knn.rerank(ds.X, H, res["idx"], k)
             torch.cuda.synchronize()
             qps = reps * H.shape[0] / (time.perf_counter() - t0)
-            table.append({"B0": B0, "B": B, "grow": grow, "threads": th, "c_alpha": chosen,
-                          "queries_per_s": round(qps, 1)})
+            row = {"B0": B0, "B": B, "grow": grow, "threads": th, "c_alpha": chosen, "queries_per_s": round(qps, 1)}
+            if g > 1:
+                row["block"] = g
+            table.append(row)
     if not table:
         raise knn.KnnError("autotune: no configuration reached the target recall")
     best = max(table, key=lambda r: r["queries_per_s"])

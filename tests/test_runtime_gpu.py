@@ -62,3 +62,20 @@ def test_autotune_picks_a_configuration_meeting_the_target(data, tmp_path):
         assert runtime.tune_key(ds, 10, "f32") in json.load(f)
     again = runtime.autotune(ds, H, 10, 0.01, cache=cache)   # served from the cache
     assert again == out
+
+
+def test_autotune_over_sampling_units(data, tmp_path):
+    """Single coordinates and 8-coordinate blocks in one search: the choice
+    meets the recall target and names its sampling unit."""
+    ds, Qd = data
+    H = Qd[96:160].contiguous()
+    out = runtime.autotune(ds, H, 10, 0.01, schedules=((8, 8, 1),), threads=(512,), blocks=(1, 8),
+                           block_schedules=((2, 2, 1),), c_grid=(1e-2, 1e-3, 1e-4), use_cache=False,
+                           cache=str(tmp_path / "t.json"))
+    assert {r.get("block", 1) for r in out["table"]} <= {1, 8} and len(out["table"]) >= 1
+    best = out["best"]
+    res = ds.adaptive(H, 10, 0.01, 0, bound="exp", c_alpha=best["c_alpha"], B0=best["B0"], B=best["B"],
+                      grow=best["grow"], threads=best["threads"], block=best.get("block", 1), qid_base=1 << 41)
+    ri, rd = knn.rerank(ds.X, H, res["idx"], 10)
+    ti, td = ds.exact(H, 10, screen="f32")
+    assert runtime.recall(ri, rd, ti, td) >= 0.999
