@@ -969,7 +969,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
 // query. Draws, lane grouping (G lanes per point, one block of 8 draws each)
 // and the shuffle reduction are those of gather_sampled, so the sums are the
 // same bit for bit. Needs B0 <= 256 (at most 32 blocks).
-constexpr int kR0Threads = 256;
+constexpr int kR0Threads = 1024;
 constexpr int kR0MaxRows = 32;
 constexpr size_t kR0SmemBudget = 110 * 1024;
 
