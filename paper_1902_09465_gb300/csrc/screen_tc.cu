@@ -11,8 +11,10 @@
 // is ||xc||^2 + ||qc||^2 - 2 xc.qc and its error bound is applied by the
 // select kernel.
 //
-// GEMM: one CTA per 128-point x 256-query tile, 128 threads. Warp 0 lane 0
-// issues TMA loads (128-byte swizzle, 64 K-elements per stage, 4 stages),
+// GEMM: one CTA per 128-point x 256-query tile, 128 threads, two CTAs per
+// SM (about 97 KB of shared memory and 256 TMEM columns each, so one CTA's
+// epilogue overlaps the other's main loop). Warp 0 lane 0 issues TMA loads
+// (128-byte swizzle, 64 K-elements per stage, 2 stages),
 // warp 1 lane 0 issues tcgen05.mma (M=128, N=256, K=16, BF16 x BF16 -> FP32
 // in TMEM) and commits each stage back to the producer; all four warps then
 // read their 32 TMEM lanes (tcgen05.ld 32x32b) and write the screened values.
@@ -40,7 +42,7 @@ knn_status launch_screen_select(float* D, int64_t n, int32_t nq, int32_t m, int3
                                 cudaStream_t stream);
 constexpr int kExactCandTc = 2048;
 
-constexpr int kTcM = 128, kTcN = 256, kTcK = 64, kTcStages = 4, kTcThreads = 128;
+constexpr int kTcM = 128, kTcN = 256, kTcK = 64, kTcStages = 2, kTcThreads = 128;
 constexpr int kTcABytes = kTcM * kTcK * 2;  // 16 KB
 constexpr int kTcBBytes = kTcN * kTcK * 2;  // 32 KB
 constexpr uint32_t kSpinLimit = 1u << 26;
@@ -122,7 +124,7 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t n,
                      int nq, int Kt, const float* __restrict__ xn, const float* __restrict__ qn, float* __restrict__ D,
                      int* status) {
