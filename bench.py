@@ -49,17 +49,24 @@ RECALL_TARGET = 0.999
 # capture of the timed configuration. It is
 # reported only while the kernel sources hash to the recorded value and the
 # launch configuration matches; otherwise the roofline's traffic is null.
-TRAFFIC_CAPTURE = {"sha1": "798ebae11331e106109508c2c20358e6b1b648cd",
+TRAFFIC_CAPTURE = {"sha1": "a4e4f07d5abf35db4042e737f01cb84442ad1b04",
                    "bytes": (0.318e9 + 0.370e9) + (21.41e9 + 1.51e9),
                    "config": {"c_alpha": 1e-3, "B0": 8, "B": 8, "grow": 1, "threads": 1024, "nq": 1024}}
 
 
 def kernel_sources_sha1():
+    """Hash of the round-loop kernel sources with comments and blank lines
+    removed: the traffic record stays valid across comment-only edits."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in ("adaptive_kernel.cuh", "knn_common.cuh"):
-        with open(os.path.join(ROOT, "paper_1902_09465_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1902_09465_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(text.encode())
     return h.hexdigest()
 
 

@@ -22,6 +22,16 @@
 //             other half of the CTA's ping-pong buffers.
 // Active points of a query all carry the same sample count T, so T is a
 // per-round scalar, and the per-point state is (id, S, Kahan term).
+//
+// Variants, each a template argument: the element type wraps the copy
+// for shared coordinates (Perm: row prefixes of a column-permuted copy) or
+// block samples (Blk: one of ceil(m/g) blocks of g coordinates per draw); a
+// bool selects the l1 distance (|x - q| terms, span-scaled widths). Round 0
+// of a dataset call comes from a point-major pass (round0_kernel for per-pair
+// draws, round0_shared_kernel for shared coordinates) that writes the
+// round-0 sums and per-tile minima; the round loop then drops the provably
+// eliminated points in one streaming pass (round0_filter) before its first
+// select.
 #pragma once
 
 #include <cuda_fp8.h>
