@@ -366,11 +366,11 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
         /* A copy's sample differs from the data's by at most e (2 |xt - q| + e),
          * so its mean over the sampled coordinates by at most e (2 mean|xt - q|
          * + e) <= e (2 sqrt(d_i) + e), d_i the copy's estimate (the mean of
-         * |z| is at most the square root of the mean of z^2). After round 0
+         * |z| is at most the square root of the mean of z^2). In every round
          * the width takes the largest estimate among the points it decides,
          * when that is below the span form. */
         double eps_r = eps;
-        if (!exact && r > 0 && emax > 0.0 && metric != ORC_METRIC_L1) {
+        if (!exact && emax > 0.0 && metric != ORC_METRIC_L1) {
             double dmax = 0.0;
             for (int64_t i = 0; i < n; ++i)
                 if (status[i] == ORC_ACTIVE && Sx[i] / Tg > dmax) dmax = Sx[i] / Tg;

@@ -760,6 +760,21 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       evals += (int64_t)nact * (exact ? (int64_t)m : Br * a.g);
       float w = exact ? 0.0f : span2 * alpha_of(a, Tn) + eps;
       const float Tf = (float)(Tn * a.g);  // estimate = S / (T g): mean per coordinate
+      // A copy's term shrinks to e (2 sqrt(d_max) + e), d_max the largest
+      // estimate among the points this round decides: a copy moves a sample by
+      // at most e (2 |x~ - q| + e), and the mean of |x~ - q| is at most the
+      // square root of the mean of (x~ - q)^2.
+      const bool shrink = !L1 && E::kStorage != KNN_STORE_F32 && !exact && ecopy > 0.0f;
+      auto copy_width = [&](float mx) {
+        const float e2 = ecopy * (2.0f * sqrtf(mx / Tf) + ecopy);
+        if (e2 < eps) w = span2 * alpha_of(a, Tn) + e2;
+      };
+      if (flt && shrink) {  // the filter needs the width first: d_max over every round-0 sum
+        const float* R0q = a.R0 + (size_t)q * (size_t)n;
+        float mx = 0.0f;
+        for (int64_t i = tid; i < n; i += NT) mx = fmaxf(mx, R0q[i]);
+        copy_width(block_max<NT>(mx, sh.bs));
+      }
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
       if (flt)
@@ -775,16 +790,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         gather_sampled<NT, E, L1>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
       const bool ident = (r == 0) && !flt;  // slot s holds point s
-      // After round 0 a copy's term shrinks to e (2 sqrt(d_max) + e), d_max the
-      // largest estimate among the points decided now: a copy moves a sample by
-      // at most e (2 |x~ - q| + e), and the mean of |x~ - q| is at most the square
-      // root of the mean of (x~ - q)^2.
-      if (!L1 && E::kStorage != KNN_STORE_F32 && r > 0 && !exact && ecopy > 0.0f) {
+      if (shrink && !flt) {  // every point of the round has its sum in Sc
         float mx = 0.0f;
         for (int i = tid; i < nact; i += NT) mx = fmaxf(mx, Sc[i]);
-        mx = block_max<NT>(mx, sh.bs);
-        const float e2 = ecopy * (2.0f * sqrtf(mx / Tf) + ecopy);
-        if (e2 < eps) w = span2 * alpha_of(a, Tn) + e2;
+        copy_width(block_max<NT>(mx, sh.bs));
       }
 
       // ---- thresholds

@@ -400,3 +400,38 @@ def test_copy_width_after_round_0_uses_the_active_estimates(target, decided):
         assert r["stats"][0]["rounds"] == 2 and list(r["idx"][0]) == [0]
     else:
         assert np.all(rounds[:3] >= 2)
+
+
+@pytest.mark.parametrize("target,decided", [("between_new_and_old", True), ("below_half_factor", False)])
+def test_copy_width_in_round_0_uses_the_active_estimates(target, decided):
+    """Closed-form case for the copy term in round 0. Query and point 0 at 0,
+    points 1 and 2 at 257 (BF16 copy 256: e = 1), point 3 alternating -2048
+    and +2048: it fixes span = 4096, yet each of its samples is 2048^2, so
+    the largest round-0 estimate is 2048^2 and the copy term is
+    e (2 * 2048 + e) = 4097 against the span form e (2 * 4096 + e) = 8193.
+    Everything is decided in round 0 (point 0 accepted, 1-3 eliminated) iff
+    w0 = span'^2 alpha(2) + 4097 is below 32768: alpha(2) is set so that this
+    holds but would fail with the span form (case 1), or so that it fails but
+    would hold with half the copy term (case 2)."""
+    n, m, delta, e, span = 4, 32, 0.01, 1.0, 4096.0
+    X = np.zeros((n, m), dtype=np.float32)
+    X[1:3] = 257.0
+    X[3, 0::2], X[3, 1::2] = -2048.0, 2048.0
+    q = np.zeros((1, m), dtype=np.float32)
+    _, _, emax = oracle.quantize(X, "bf16")
+    assert emax == e
+    sp2 = (span + 2 * e) ** 2
+    lg = lambda u: math.log(1.0 + (1.0 + math.log(u)) * n / delta)
+    if target == "between_new_and_old":
+        a2 = (32768 - 0.5 * (4097 + 8193)) / sp2
+    else:
+        a2 = (32768 - 0.5 * (4097 + 2049)) / sp2
+    c = a2 * a2 * 2 / lg(2)
+    r = oracle.adaptive(X, q, oracle.make_params(1, h=0, delta=delta, bound="exp", c_alpha=c, B0=2, B=2,
+                                                 storage="bf16"))
+    rounds = r["code"][0] >> 2
+    if decided:
+        assert r["stats"][0]["rounds"] == 1 and list(r["idx"][0]) == [0]
+        assert np.all(rounds == 0) and np.all((r["code"][0][1:] & 3) == oracle.ELIMINATED)
+    else:
+        assert r["stats"][0]["rounds"] >= 2 and np.all(rounds[:3] >= 1)

@@ -61,6 +61,19 @@ def test_copies_gaussian_and_ragged_dims(storage):
             replay(X, Q, ds, storage, 4, bound="exp", c_alpha=1e-3, B0=8, B=8, grow=1)
 
 
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+@pytest.mark.parametrize("n,k", [(200, 20), (6000, 5)])
+def test_round0_copy_width_from_largest_estimate(storage, n, k):
+    """N(0,1)-like data, where the largest round-0 estimate sits well below
+    the squared span: round 0 takes the copy term from it. n = 200 with k = 20
+    has fewer tiles of round-0 minima than k (no round-0 filter: the maximum
+    comes from the round's sums); n = 6000 runs the filter (the maximum over
+    every round-0 sum, before it drops points)."""
+    X, Q, _ = synth.gaussian_planted(n, 256, k, nq=4, seed=n + k)
+    with knn.Dataset(torch.from_numpy(X).cuda(), copies=(storage,)) as ds:
+        replay(X, Q, ds, storage, k, h=min(k, n - k), bound="exp", c_alpha=1e-3, B0=16, B=16, grow=1)
+
+
 def test_f32_dataset_equals_knn_adaptive():
     X, Q = synth.pixel_mixture(8000, 256, 8, seed=3)
     Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
