@@ -51,6 +51,7 @@ RECALL_TARGET = 0.999
 # launch configuration matches; otherwise the roofline's traffic is null.
 TRAFFIC_CAPTURE = {"sha1": "20ba59b1b852ce691ce659ba0ce74bcc9bf5c6cf",
                    "bytes": (0.317e9 + 0.370e9) + (21.38e9 + 1.50e9),
+                   "rounds_bytes": 21.38e9 + 1.50e9, "rounds_ms": 5.84,  # the round-loop kernel alone
                    "config": {"c_alpha": 1e-3, "B0": 8, "B": 8, "grow": 1, "threads": 1024, "nq": 1024}}
 
 
@@ -751,10 +752,15 @@ def run_figure2(args):
 def run_profile_step(args):
     """The timed step alone, for profilers: the benchmark workload with the
     options given on the command line (no autotuning, no variants), W
-    warm-up steps then K steps of the CUDA graph (rounds + rerank)."""
+    warm-up steps then K steps of the CUDA graph (rounds + rerank). With
+    --phases it loads the phase-timing build of the library and reports the
+    share of the round loop's CTA clocks spent in each phase."""
     import torch
     from paper_1902_09465_gb300 import knn, runtime
 
+    if args.phases:
+        from paper_1902_09465_gb300 import build
+        knn.use_library(build.build(phase_timing=True))
     torch.cuda.set_device(0)
     w = WORKLOAD
     X, Q, _ = make_inputs(0)
@@ -769,15 +775,46 @@ def run_profile_step(args):
     for _ in range(args.warmup):
         step.run(Qd)
     torch.cuda.synchronize()
+    if args.phases:
+        knn.phase_clocks(reset=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
         res, ri, rd = step.run(Qd)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_step": w["name"], "storage": args.storage, "shared": args.share, **opts,
-                      "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 4),
-                      "evals": int(res["evals"].sum().item())}), flush=True)
+    out = {"profile_step": w["name"], "storage": args.storage, "shared": args.share, **opts,
+           "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 4), "evals": int(res["evals"].sum().item())}
+    if args.phases:
+        out.update(phase_report(knn.phase_clocks(), opts, args, w))
+    print(json.dumps(out), flush=True)
+
+
+def phase_report(clk, opts, args, w):
+    """Shares of the round loop's CTA clocks per phase and, for the captured
+    configuration, the DRAM rate of its gather phases: the round loop's
+    captured DRAM bytes less the round-0 filter's read of the round-0 sums
+    (4 B per pair), over the captured kernel time times the gather phases'
+    share. The shares count the clocks of working CTAs, so share x kernel
+    time is at least the gathers' wall time and the rate is a lower bound."""
+    tot = sum(clk["rounds"].values()) + sum(clk["round0"].values())
+    shares = {"rounds": {k: round(v / tot, 4) for k, v in clk["rounds"].items()},
+              "round0": {k: round(v / tot, 4) for k, v in clk["round0"].items()}}
+    out = {"phase_clock_shares": shares, "phase_clocks_total": tot, "note": "phase-timing build (a barrier per "
+           "query and one thread's atomics added): shares, not times"}
+    g = shares["rounds"]["gather"] + shares["rounds"]["exact"]
+    cfg = {"c_alpha": opts["c_alpha"], "B0": opts["B0"], "B": opts["B"], "grow": opts["grow"],
+           "threads": opts["threads"], "nq": w["nq"]}
+    rc = TRAFFIC_CAPTURE
+    if (cfg == rc["config"] and args.storage == "f32" and not args.share and args.block == 1
+            and kernel_sources_sha1() == rc["sha1"]):
+        gbytes = rc["rounds_bytes"] - 4.0 * w["n"] * w["nq"]
+        rate = gbytes / (rc["rounds_ms"] * 1e-3 * g) / 1e9
+        hbm, kind = peaks()
+        out["gather_phase_dram"] = {"bytes": gbytes, "share": round(g, 4), "kernel_ms": rc["rounds_ms"],
+                                    "gbs_at_least": round(rate, 1), "peak": hbm, "frac_at_least": round(rate / hbm, 4),
+                                    "peak_kind": kind}
+    return out
 
 
 def main():
@@ -802,6 +839,8 @@ def main():
     ap.add_argument("--block", type=int, default=1)
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
     ap.add_argument("--share", action="store_true", help="shared coordinates (both counter masks zero)")
+    ap.add_argument("--phases", action="store_true",
+                    help="with --profile-step: phase-timing build, per-phase shares of the round loop")
     ap.add_argument("--sweep-gaps", dest="sweep_gaps", default=None, help="comma-separated gap ratios")
     ap.add_argument("--sweep-variants", dest="sweep_variants", default=None, help="comma-separated variant names")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=5.0)

@@ -299,6 +299,18 @@ knn_status knn_exact_ds(const knn_dataset* ds, int32_t screen, const float* Q, i
  * Waits for the device, then clears the status. */
 knn_status knn_device_status(int32_t* out);
 
+/* Clock totals of the phases of the adaptive round-loop kernel, summed over
+ * its CTAs (SM clock cycles seen by each CTA's first thread between phase
+ * boundaries; tracing, not part of the method). out: 16 host uint64_t:
+ *   [0] setup  [1] sampled gathers  [2] exact rows  [3] select
+ *   [4] thresholds  [5] decide + compact  [6] output (per query)
+ * for the rounds after round 0, and [8..13] phases 0-5 of round 0 ([9] is the
+ * round-0 filter when the point-major pass ran). reset != 0 zeroes the totals
+ * after reading. Waits for the device. Only a library compiled with
+ * KNN_PHASE_TIMING records them (a separate build: the timing adds a barrier
+ * per query and atomics by one thread); any other returns KNN_EUNSUPPORTED. */
+knn_status knn_phase_clocks(uint64_t* out, int32_t reset);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* knn_last_error(void);
 

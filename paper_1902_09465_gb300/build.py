@@ -3,6 +3,11 @@
 Each ``csrc/*.cu`` translation unit is compiled by its own nvcc process (in
 parallel), then linked into one shared library next to this file. No torch,
 no cmake: the library has a plain C ABI (``include/knn_gb300.h``).
+
+``build(phase_timing=True)`` builds a second library,
+``libknn_gb300_phases.so``, compiled with ``KNN_PHASE_TIMING``: the round-loop
+kernel then records per-phase clock totals (``knn_phase_clocks``). It is a
+tracing build for measurement, never the default.
 """
 
 from __future__ import annotations
@@ -18,6 +23,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libknn_gb300.so")
+BUILD_PHASES = os.path.join(HERE, "_build_phases")
+LIB_PHASES = os.path.join(HERE, "libknn_gb300_phases.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,13 +44,13 @@ def _deps():
     return out
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, verbose_ptxas: bool, build_dir: str = BUILD, defines=()) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(d) for d in _deps()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not verbose_ptxas:
         return obj
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", src, "-o", obj + ".tmp",
-           "-I", os.path.join(ROOT, "include")]
+           "-I", os.path.join(ROOT, "include"), *[f"-D{d}" for d in defines]]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,20 +62,22 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose_ptxas: bool = False, phase_timing: bool = False) -> str:
+    build_dir, lib = (BUILD_PHASES, LIB_PHASES) if phase_timing else (BUILD, LIB)
+    defines = ("KNN_PHASE_TIMING",) if phase_timing else ()
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(16, max(4, os.cpu_count() or 4), len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, build_dir, defines), srcs))
+    if not os.path.exists(lib) or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose_ptxas="-v" in sys.argv))
+    print(build(verbose_ptxas="-v" in sys.argv, phase_timing="--phases" in sys.argv))

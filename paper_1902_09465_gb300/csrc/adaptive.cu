@@ -112,6 +112,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.r0tiles = 0;
   a.jperm = nullptr;
   a.mp = 0;
+  a.phase_clk = phase_clocks_ptr();
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;
@@ -270,6 +271,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.r0tiles = 0;
   a.jperm = nullptr;
   a.mp = 0;
+  a.phase_clk = phase_clocks_ptr();
   a.bound = o.bound;
   const double dprime = delta / (double)n;
   a.a_c0 = 0.0f;

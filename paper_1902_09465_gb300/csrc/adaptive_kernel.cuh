@@ -91,7 +91,38 @@ struct AdaptiveArgs {
   int32_t r0tiles;      // tiles per query in R0min
   const int32_t* jperm; // shared-coordinate copies: column of draw t (t < m), for Perm element types
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
+  unsigned long long* phase_clk;  // per-phase clock totals [16] (libraries built with phase timing; else null)
 };
+
+// Phase timing (compiled in only with KNN_PHASE_TIMING): thread 0 of each CTA
+// adds the SM clocks spent since the previous boundary to phase i of
+// phase_clk; phases of round 0 go to i + 8 (the output phase stays at 6).
+#ifdef KNN_PHASE_TIMING
+#define KNN_PHASE_START long long phase_t0_ = clock64()
+#define KNN_PHASE(i)                                                                                 \
+  do {                                                                                               \
+    if (threadIdx.x == 0 && a.phase_clk) {                                                           \
+      const long long t_ = clock64();                                                                \
+      atomicAdd(a.phase_clk + (i) + ((r) == 0 && (i) != 6 ? 8 : 0), (unsigned long long)(t_ - phase_t0_)); \
+      phase_t0_ = t_;                                                                                \
+    }                                                                                                \
+  } while (0)
+#define KNN_PHASE_SYNC(i) \
+  do {                    \
+    __syncthreads();      \
+    KNN_PHASE(i);         \
+  } while (0)
+#else
+#define KNN_PHASE_START \
+  do {                  \
+  } while (0)
+#define KNN_PHASE(i) \
+  do {               \
+  } while (0)
+#define KNN_PHASE_SYNC(i) \
+  do {                    \
+  } while (0)
+#endif
 
 // Element access of the gathered copy. A stored BF16 value is the top half of
 // the FP32 word; an FP8 e4m3 value is converted exactly and multiplied by its
@@ -667,6 +698,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   float* acc_d = a.ws_acc_d + slot * (size_t)a.acc_cap;
   float* acc_U = a.ws_acc_U + slot * (size_t)a.acc_cap;
   float* acc_L = a.ws_acc_L + slot * (size_t)a.acc_cap;
+  KNN_PHASE_START;
 
   for (;;) {
     if (tid == 0) sh.q = atomicAdd(a.queue, 1);
@@ -777,6 +809,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       }
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
+      KNN_PHASE(0);  // setup
       if (flt)
         nact = round0_filter<NT>(a, q, n, k, w, Tf, hist, buf, sh, ids0 + (size_t)cur * n, Sc,
                                  ids0 + (size_t)(cur ^ 1) * n, S0 + (size_t)(cur ^ 1) * n, lcode, lS, &min_elim);
@@ -789,6 +822,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       else
         gather_sampled<NT, E, L1>(a, qid, r, nact, T, Tn, E::kPerm ? qsp : qs, idc, Sc, Cc, hist);
       __syncthreads();
+      if (exact) KNN_PHASE(2); else KNN_PHASE(1);  // exact rows / sampled gathers (round 0: the filter)
       const bool ident = (r == 0) && !flt;  // slot s holds point s
       if (shrink && !flt) {  // every point of the round has its sum in Sc
         float mx = 0.0f;
@@ -806,12 +840,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       }
       if (tid == 0) sh.nacc_add = 0;
       __syncthreads();
+      KNN_PHASE(3);  // select
       const float tauU = kth_of_union<NT>(actU, min(k, nact), acc_U, nacc, k, &sh.tauU);
       // (after the round-0 filter the kept points can number k: the (k+1)-th
       // smallest LCB is then that of a dropped point, min_elim)
       const float tauL = nact + nacc > k ? fminf(kth_of_union<NT>(actL, kk, acc_L, nacc, k + 1, &sh.tauL), min_elim)
                                          : min_elim;
 
+      KNN_PHASE(4);  // thresholds
       // ---- decide + compact (order-preserving)
       int32_t* idn = ids0 + (size_t)(cur ^ 1) * n;
       float* Sn = S0 + (size_t)(cur ^ 1) * n;
@@ -877,6 +913,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         out_base += total;
       }
       rmin = block_min<NT>(rmin, sh.bs);  // also orders sh.nacc_add
+      KNN_PHASE(5);  // decide + compact
       nacc = min(nacc + sh.nacc_add, a.acc_cap);
       nact = out_base;
       min_elim = fminf(min_elim, rmin);
@@ -972,6 +1009,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         lcode[idf[i]] = 4 * r + 0;
         if (lS) lS[idf[i]] = Sf[i];
       }
+    KNN_PHASE_SYNC(6);  // output
     if (tid == 0) {
       a.out_count[q] = count;
       a.out_evals[q] = evals;

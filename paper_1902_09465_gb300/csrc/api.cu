@@ -99,7 +99,31 @@ knn_status device_status_ptr(int** out) {
   return KNN_OK;
 }
 
+#ifdef KNN_PHASE_TIMING
+// Phase clock totals of the round-loop kernel (see knn_phase_clocks).
+static __device__ unsigned long long g_phase_clk[16];
+
+unsigned long long* phase_clocks_ptr() {
+  void* p = nullptr;
+  return cudaGetSymbolAddress(&p, g_phase_clk) == cudaSuccess ? static_cast<unsigned long long*>(p) : nullptr;
+}
+#else
+unsigned long long* phase_clocks_ptr() { return nullptr; }
+#endif
+
 }  // namespace knn
+
+extern "C" knn_status knn_phase_clocks(uint64_t* out, int32_t reset) {
+  knn::clear_error();
+  if (!out) return knn::set_error("knn_phase_clocks: null pointer"), KNN_EINVAL;
+  unsigned long long* p = knn::phase_clocks_ptr();
+  if (!p) return knn::set_error("knn_phase_clocks: library built without phase timing"), KNN_EUNSUPPORTED;
+  unsigned long long v[16];
+  knn_status s = knn::cuda_check(cudaMemcpy(v, p, sizeof(v), cudaMemcpyDeviceToHost), "read phase clocks");
+  if (s == KNN_OK && reset) s = knn::cuda_check(cudaMemset(p, 0, sizeof(v)), "clear phase clocks");
+  for (int i = 0; i < 16; ++i) out[i] = (uint64_t)v[i];
+  return s;
+}
 
 extern "C" knn_status knn_device_status(int32_t* out) {
   knn::clear_error();

@@ -114,6 +114,7 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   a.r0tiles = tiles;
   a.jperm = ds->jperm;
   a.mp = ds->mp;
+  a.phase_clk = phase_clocks_ptr();
   if (r0 && !E::kPerm) {
     s = cuda_check(cudaFuncSetAttribute(a.l1 ? reinterpret_cast<const void*>(round0_kernel<E, true>)
                                              : reinterpret_cast<const void*>(round0_kernel<E, false>),

@@ -54,6 +54,10 @@ struct Workspace {
 // wait record a code here (read and cleared by knn_device_status).
 knn_status device_status_ptr(int** out);
 
+// Device address of the round-loop phase clock totals of the current device
+// (16 counters) in a library built with KNN_PHASE_TIMING; null otherwise.
+unsigned long long* phase_clocks_ptr();
+
 }  // namespace knn
 
 // A resident dataset (see knn_dataset_create).

@@ -59,6 +59,7 @@ _SIGS = {
     "knn_exact_ds_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32]),
     "knn_exact_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "knn_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
+    "knn_phase_clocks": (C.c_int, [C.POINTER(C.c_uint64), C.c_int32]),
     "knn_adaptive_ds_multi_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32, C.POINTER(Opts)]),
     "knn_adaptive_ds_multi": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_double, C.c_uint64,
                                         C.POINTER(Opts), _P, _P, _P, _P, _P, C.c_size_t, _P]),
@@ -66,6 +67,16 @@ _SIGS = {
     "knn_last_error": (C.c_char_p, []),
     "knn_version": (C.c_char_p, []),
 }
+
+
+def use_library(path: str) -> None:
+    """Load ``path`` (a build of the same library, e.g. the phase-timing one)
+    in place of the default; only before the first call into the library."""
+    global LIB_PATH
+    with _lock:
+        if _lib is not None:
+            raise KnnError("the library is already loaded")
+        LIB_PATH = path
 
 
 def lib():
@@ -335,6 +346,18 @@ def device_status() -> int:
     v = C.c_int32()
     _check(lib().knn_device_status(C.byref(v)))
     return int(v.value)
+
+
+PHASES = ("setup", "gather", "exact", "select", "thresholds", "decide_compact", "output")
+
+
+def phase_clocks(reset: bool = False) -> dict:
+    """Round-loop phase clock totals (a library built with phase timing only;
+    the default one raises): {"rounds": {phase: clocks}, "round0": {...}}."""
+    v = (C.c_uint64 * 16)()
+    _check(lib().knn_phase_clocks(v, 1 if reset else 0))
+    return {"rounds": {name: int(v[i]) for i, name in enumerate(PHASES)},
+            "round0": {name: int(v[8 + i]) for i, name in enumerate(PHASES[:6])}}
 
 
 def version() -> str:

@@ -76,6 +76,20 @@ def test_invalid_arguments_are_rejected_on_the_host(lib_path):
     assert o2.block == 1 and o2.metric == 0
 
 
+def test_phase_clocks_only_in_the_timing_build(lib_path):
+    """The default library has no phase timing: the call is refused on the
+    host (no device work); the binding refuses to swap a loaded library."""
+    from paper_1902_09465_gb300 import knn
+    L = knn.lib()
+    v = (ctypes.c_uint64 * 16)()
+    assert L.knn_phase_clocks(v, 0) == 4 and "phase timing" in L.knn_last_error().decode()
+    assert L.knn_phase_clocks(None, 0) == 1
+    with pytest.raises(knn.KnnError):
+        knn.phase_clocks()
+    with pytest.raises(knn.KnnError):
+        knn.use_library(lib_path)
+
+
 def test_oracle_and_library_share_no_code():
     lib_src = glob.glob(os.path.join(ROOT, "paper_1902_09465_gb300", "**", "*"), recursive=True)
     for f in lib_src:
