@@ -25,6 +25,7 @@ STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
 COPY_SCREEN = 1 << 3
 SCREENS = {"f32": 0, "bf16x3": 1}
 ACTIVE, ELIMINATED, ACCEPTED = 0, 1, 2
+MAX_KH = 1024  # largest k + h (candidate set size) the library accepts
 FULL_MASK = (1 << 64) - 1
 
 

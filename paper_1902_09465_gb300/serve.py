@@ -93,6 +93,20 @@ class Server:
 
     # -- request flow
     def submit(self, req: Request):
+        """Queues a request. A malformed one is refused here, before it can
+        reach a launch that other requests share."""
+        if not 0 <= req.dataset < len(self.datasets):
+            raise ValueError(f"request {req.rid}: no dataset {req.dataset}")
+        ds, cfg = self.datasets[req.dataset], self.configs[req.dataset]
+        Q = req.Q
+        if not isinstance(Q, torch.Tensor) or Q.dim() != 2 or Q.dtype != torch.float32 or Q.is_cuda:
+            raise ValueError(f"request {req.rid}: Q must be a 2-D float32 host tensor")
+        if Q.shape[0] < 1 or Q.shape[1] != ds.m:
+            raise ValueError(f"request {req.rid}: Q is {tuple(Q.shape)}, the dataset has m = {ds.m}")
+        # the adaptive engine returns k + h = 2k candidates per query
+        k_cap = min(ds.n, knn.MAX_KH if cfg.method == "exact" else knn.MAX_KH // 2)
+        if not 1 <= req.k <= k_cap:
+            raise ValueError(f"request {req.rid}: k = {req.k} outside [1, {k_cap}]")
         if req.t_arrival == 0.0:
             req.t_arrival = time.perf_counter()
         self.queue.append(req)
