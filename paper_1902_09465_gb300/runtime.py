@@ -103,13 +103,15 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
     the smallest C_alpha of the grid whose recall on the held-out queries H
     (after the FP64 rerank) is at least target + margin, then the fastest of
     those. Returns a dict with the choice and the whole table, and stores it
-    in the JSON cache under a key of (d, n bucket, storage, k, options).
+    in the JSON cache under a key of (d, n bucket, storage, k, delta, the
+    recall target and margin, options).
     `extra` adds options to every call (for example the shared-coordinate
     masks); `seed` is the Philox seed used."""
     path = _cache_path(cache)
     extra = dict(extra or {})
     blocks = tuple(int(g) for g in blocks)
-    key = tune_key(ds, k, storage) + ("|" + ",".join(f"{a}={b}" for a, b in sorted(extra.items())) if extra else "")
+    key = tune_key(ds, k, storage) + f"|delta={delta:g}|target={target:g}+{margin:g}"
+    key += ("|" + ",".join(f"{a}={b}" for a, b in sorted(extra.items())) if extra else "")
     if blocks != (1,):
         key += "|blocks=" + ",".join(str(g) for g in blocks)
     if use_cache and os.path.exists(path):
@@ -162,9 +164,10 @@ def autotune(ds: knn.Dataset, H: torch.Tensor, k: int, delta: float = 0.01, stor
             with open(path) as f:
                 data = json.load(f)
         data[key] = out
-        with open(path + ".tmp", "w") as f:
+        tmp = f"{path}.tmp{os.getpid()}"
+        with open(tmp, "w") as f:
             json.dump(data, f, indent=1)
-        os.replace(path + ".tmp", path)
+        os.replace(tmp, path)
     except (OSError, ValueError):
         pass
     return out

@@ -59,7 +59,8 @@ def test_autotune_picks_a_configuration_meeting_the_target(data, tmp_path):
     ti, td = ds.exact(H, 10, screen="f32")
     assert runtime.recall(ri, rd, ti, td) >= 0.999
     with open(cache) as f:
-        assert runtime.tune_key(ds, 10, "f32") in json.load(f)
+        assert out["key"] in json.load(f)
+    assert out["key"].startswith(runtime.tune_key(ds, 10, "f32")) and "target=0.999+" in out["key"]
     again = runtime.autotune(ds, H, 10, 0.01, cache=cache)   # served from the cache
     assert again == out
 
