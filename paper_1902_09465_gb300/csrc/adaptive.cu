@@ -38,7 +38,6 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
     const size_t chunk = (size_t)round0_chunk(n, nq, p.grid);
     cv.take<float>(chunk * (size_t)n);                                      // round-0 sums
     cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // their tile minima
-    cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // and maxima (copies)
     cv.take<float>(chunk * 64);                                             // permuted query columns
   }
   return cv.off + 256;
@@ -110,7 +109,6 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.out_stride = k + o.h;
   a.R0 = nullptr;
   a.R0min = nullptr;
-  a.R0max = nullptr;
   a.r0tiles = 0;
   a.jperm = nullptr;
   a.mp = 0;
@@ -270,7 +268,6 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.out_stride = k + o.h;
   a.R0 = nullptr;
   a.R0min = nullptr;
-  a.R0max = nullptr;
   a.r0tiles = 0;
   a.jperm = nullptr;
   a.mp = 0;

@@ -89,7 +89,6 @@ struct AdaptiveArgs {
   const float* R0;      // round-0 sums [nq][n] precomputed by round0_kernel (null: round 0 samples in place)
   const float* R0min;   // smallest round-0 sum of each tile of points [nq][r0tiles] (null: no filter)
   int32_t r0tiles;      // tiles per query in R0min
-  const float* R0max;   // largest round-0 sum of each tile [nq][r0tiles] (stored copies only; else null)
   const int32_t* jperm; // shared-coordinate copies: column of draw t (t < m), for Perm element types
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
   unsigned long long* phase_clk;  // per-phase clock totals [16] (libraries built with phase timing; else null)
@@ -803,14 +802,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         if (e2 < eps) w = span2 * alpha_of(a, Tn) + e2;
       };
       if (flt && shrink) {  // the filter needs the width first: d_max over every round-0 sum
+        const float* R0q = a.R0 + (size_t)q * (size_t)n;
         float mx = 0.0f;
-        if (a.R0max) {  // from the round-0 pass's tile maxima
-          const float* mq = a.R0max + (size_t)q * (size_t)a.r0tiles;
-          for (int i = tid; i < a.r0tiles; i += NT) mx = fmaxf(mx, mq[i]);
-        } else {
-          const float* R0q = a.R0 + (size_t)q * (size_t)n;
-          for (int64_t i = tid; i < n; i += NT) mx = fmaxf(mx, R0q[i]);
-        }
+        for (int64_t i = tid; i < n; i += NT) mx = fmaxf(mx, R0q[i]);
         copy_width(block_max<NT>(mx, sh.bs));
       }
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
@@ -1043,7 +1037,7 @@ static inline int round0_rows(int m) {
 
 template <class E, bool L1>
 __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int rows_per_cta, float* R0,
-                                                            float* R0min, float* R0max) {
+                                                            float* R0min) {
   extern __shared__ __align__(16) float rows[];
   using Tp = typename E::T;
   const int m = a.m;
@@ -1069,7 +1063,6 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
     const uint64_t qfield = qid & a.mask_q;
     const float* qr = a.Q + (size_t)q * m;
     float tmin = INFINITY;  // smallest sum of this CTA's rows for query q
-    float tmax = 0.0f;      // and the largest (sums are non-negative)
     for (int base = 0; base < np; base += ppw) {
       const int pi = base + grp;
       float part = 0.0f;
@@ -1117,18 +1110,12 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
       if (pi < np && gl == 0) {
         R0[(size_t)q * (size_t)n + p0 + pi] = part;
         tmin = fminf(tmin, part);
-        tmax = fmaxf(tmax, part);
       }
     }
     if (R0min) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
       if (lane == 0) R0min[(size_t)q * gridDim.x + blockIdx.x] = tmin;
-    }
-    if (R0max) {
-#pragma unroll
-      for (int o = 16; o; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-      if (lane == 0) R0max[(size_t)q * gridDim.x + blockIdx.x] = tmax;
     }
   }
 }
@@ -1197,7 +1184,7 @@ __device__ __forceinline__ float r0_shared_sum(const float* x, const float4* v4,
 
 template <class E, int NB, bool L1>
 __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(AdaptiveArgs a, const float* Qp, float* R0,
-                                                                         float* R0min, float* R0max) {
+                                                                         float* R0min) {
   // grid: x = tiles of kR0SharedThreads points, y = slices of kQ queries
   constexpr int W = 8 * NB;
   constexpr int kQ = R0SharedCfg<NB>::kQueries;
@@ -1240,12 +1227,6 @@ __global__ void __launch_bounds__(kR0SharedThreads) round0_shared_kernel(Adaptiv
 #pragma unroll
       for (int o = 16; o; o >>= 1) t = fminf(t, __shfl_xor_sync(0xffffffffu, t, o));
       if ((threadIdx.x & 31) == 0) R0min[(size_t)qg * (size_t)a.r0tiles + (size_t)(i >> 5)] = t;
-    }
-    if (R0max) {  // and the largest (sums are non-negative)
-      float t = i < n ? S : 0.0f;
-#pragma unroll
-      for (int o = 16; o; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
-      if ((threadIdx.x & 31) == 0) R0max[(size_t)qg * (size_t)a.r0tiles + (size_t)(i >> 5)] = t;
     }
   };
   int qq = 0;

@@ -37,13 +37,10 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
   const int qpw = E::kPerm && r0 ? (o.B0 <= 16 ? 16 : (o.B0 <= 32 ? 32 : 64)) : 0;  // staged by round 0
-  // tile maxima too for a stored copy: the copy term of round 0's width
-  const bool r0mx = r0 && E::kStorage != KNN_STORE_F32;
   if (r0) {
     measure.take<float>((size_t)chunk * (size_t)n);
     measure.take<float>((size_t)chunk * (size_t)tiles);
     measure.take<float>((size_t)chunk * (size_t)qpw);
-    if (r0mx) measure.take<float>((size_t)chunk * (size_t)tiles);
   }
   const size_t need = measure.off + 256;
   Workspace ws;
@@ -56,7 +53,6 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   float* r0buf = r0 ? cv.take<float>((size_t)chunk * (size_t)n) : nullptr;
   float* r0min = r0 ? cv.take<float>((size_t)chunk * (size_t)tiles) : nullptr;
   float* qperm = qpw ? cv.take<float>((size_t)chunk * (size_t)qpw) : nullptr;
-  float* r0max = r0mx ? cv.take<float>((size_t)chunk * (size_t)tiles) : nullptr;
   AdaptiveArgs a;
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
@@ -115,7 +111,6 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   set_blocks<E>(a, o);
   a.R0 = r0buf;
   a.R0min = r0min;
-  a.R0max = r0max;
   a.r0tiles = tiles;
   a.jperm = ds->jperm;
   a.mp = ds->mp;
@@ -157,21 +152,21 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
         if (o.B0 <= 16) {
           const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<2>::kQueries - 1) / R0SharedCfg<2>::kQueries));
           (a.l1 ? round0_shared_kernel<E, 2, true> : round0_shared_kernel<E, 2, false>)
-              <<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min, r0max);
+              <<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
         } else if (o.B0 <= 32) {
           const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<4>::kQueries - 1) / R0SharedCfg<4>::kQueries));
           (a.l1 ? round0_shared_kernel<E, 4, true> : round0_shared_kernel<E, 4, false>)
-              <<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min, r0max);
+              <<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
         } else {
           const dim3 grid(blocks, (unsigned)((ac.nq + R0SharedCfg<8>::kQueries - 1) / R0SharedCfg<8>::kQueries));
           (a.l1 ? round0_shared_kernel<E, 8, true> : round0_shared_kernel<E, 8, false>)
-              <<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min, r0max);
+              <<<grid, kR0SharedThreads, 0, stream>>>(ac, qperm, r0buf, r0min);
         }
         s = cuda_check(cudaGetLastError(), "round0_shared_kernel launch");
       } else {
         const unsigned blocks = (unsigned)((n + rows - 1) / rows);
         (a.l1 ? round0_kernel<E, true> : round0_kernel<E, false>)
-            <<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf, r0min, r0max);
+            <<<blocks, kR0Threads, (size_t)rows * m * 4, stream>>>(ac, rows, r0buf, r0min);
         s = cuda_check(cudaGetLastError(), "round0_kernel launch");
       }
     }
