@@ -187,7 +187,6 @@ def run_ours(args, rank, world, local_rank):
     Qd = torch.from_numpy(Q).to(dev)
     Hd = torch.from_numpy(H).to(dev)
     stream = torch.cuda.current_stream()
-    B0, B, grow = args.B0, args.B, args.grow
 
     ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen"))
 
@@ -474,14 +473,26 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-def cpu_baseline(args, budget_s=15.0, X=None, Q=None):
+def oracle_schedule(args, cfg=None):
+    """Schedule and C_alpha the oracle runs with: the GPU arm's choice (its
+    bench line's config) when given, else the autotuner's recorded choice on
+    this workload; --cpu-c-alpha / --B0 / --B / --grow, when given, override."""
+    c = dict(cfg or TRAFFIC_CAPTURE["config"])
+    out = {"c_alpha": c["c_alpha"], "B0": c["B0"], "B": c["B"], "grow": c["grow"]}
+    for key, val in (("c_alpha", args.cpu_c_alpha), ("B0", args.B0), ("B", args.B), ("grow", args.grow)):
+        if val is not None:
+            out[key] = val
+    return out
+
+
+def cpu_baseline(args, budget_s=15.0, X=None, Q=None, cfg=None):
     import oracle
     w = WORKLOAD
     if X is None:
         X, Q, _ = make_inputs(0)
     threads = int(os.environ.get("ORACLE_THREADS", "0")) or len(os.sched_getaffinity(0))
-    p = oracle.make_params(w["k"], delta=w["delta"], bound="exp", c_alpha=args.cpu_c_alpha, B0=args.B0, B=args.B,
-                           grow=args.grow, seed=0)
+    sch = oracle_schedule(args, cfg)
+    p = oracle.make_params(w["k"], delta=w["delta"], bound="exp", seed=0, **sch)
     done, t0 = 0, time.perf_counter()
     batch = threads
     while time.perf_counter() - t0 < budget_s and done < Q.shape[0]:
@@ -489,8 +500,8 @@ def cpu_baseline(args, budget_s=15.0, X=None, Q=None):
         done += batch
     dt = time.perf_counter() - t0
     return {"value": round(done / dt, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": f"{done} of {Q.shape[0]} queries (first ones), C_alpha={args.cpu_c_alpha}, "
-                      f"FP64, OpenMP over queries, {dt:.1f} s"}
+            "sample": f"{done} of {Q.shape[0]} queries (first ones), C_alpha={sch['c_alpha']}, "
+                      f"B0={sch['B0']} B={sch['B']} grow={sch['grow']}, FP64, OpenMP over queries, {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -500,8 +511,8 @@ def run_reference(args, rank, world):
     w = WORKLOAD
     X, Q, _ = make_inputs(0)
     threads = len(os.sched_getaffinity(0))
-    p = oracle.make_params(w["k"], delta=w["delta"], bound="exp", c_alpha=args.cpu_c_alpha, B0=args.B0, B=args.B,
-                           grow=args.grow, seed=0)
+    sch = oracle_schedule(args)
+    p = oracle.make_params(w["k"], delta=w["delta"], bound="exp", seed=0, **sch)
     per_step = threads  # a bounded sample of the batch per step
     for s in range(args.warmup):
         oracle.adaptive(X, Q[:per_step], p, want_state=False, threads=threads)
@@ -516,8 +527,7 @@ def run_reference(args, rank, world):
     return {"metric": METRIC, "value": round(v, 4), "unit": "queries/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "c_alpha": args.cpu_c_alpha, "B0": args.B0, "B": args.B,
-                       "grow": args.grow, "sample_per_step": per_step},
+            "config": {"workload": w["name"], **sch, "sample_per_step": per_step},
             "cpu_baseline": {"value": round(v, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
                              "sample": f"{per_step} queries per step of the {w['nq']}-query batch"},
             "e2e": {"value": round(v, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -766,7 +776,9 @@ def run_profile_step(args):
     X, Q, _ = make_inputs(0)
     Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
     ds = knn.Dataset(Xd, copies=() if args.storage == "f32" else (args.storage,))
-    opts = dict(bound="exp", c_alpha=args.c_alpha or 1e-3, B0=args.B0, B=args.B, grow=args.grow, threads=args.threads,
+    dflt = lambda v, d: d if v is None else v
+    opts = dict(bound="exp", c_alpha=args.c_alpha or 1e-3, B0=dflt(args.B0, 16), B=dflt(args.B, 16),
+                grow=dflt(args.grow, 1), threads=args.threads,
                 block=args.block)
     if args.share:
         ds.share(0, copies=(args.storage,))
@@ -824,10 +836,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--c-alpha", dest="c_alpha", type=float, default=None)
-    ap.add_argument("--cpu-c-alpha", dest="cpu_c_alpha", type=float, default=1e-3)
-    ap.add_argument("--B0", type=int, default=16)
-    ap.add_argument("--B", type=int, default=16)
-    ap.add_argument("--grow", type=int, default=1)
+    ap.add_argument("--cpu-c-alpha", dest="cpu_c_alpha", type=float, default=None,
+                    help="oracle C_alpha (default: the GPU arm's tuned choice)")
+    ap.add_argument("--B0", type=int, default=None, help="oracle / --profile-step schedule (default: tuned; 16)")
+    ap.add_argument("--B", type=int, default=None)
+    ap.add_argument("--grow", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nq", type=int, default=None, help="queries per GPU (default 1024)")
     ap.add_argument("--serve", action="store_true", help="run the serving workload instead")
@@ -892,7 +905,7 @@ def main():
     res = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(args)
+            res["cpu_baseline"] = cpu_baseline(args, cfg=res["config"])
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist
