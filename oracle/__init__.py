@@ -44,7 +44,8 @@ class AdaptiveParams(C.Structure):
     _fields_ = [("k", C.c_int32), ("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double),
                 ("delta", C.c_double), ("B0", C.c_int32), ("B", C.c_int32), ("grow", C.c_int32),
                 ("seed", C.c_uint64), ("qid", C.c_uint64), ("mask_p", C.c_uint64), ("mask_q", C.c_uint64),
-                ("tol", C.c_double), ("storage", C.c_int32), ("block", C.c_int32), ("metric", C.c_int32)]
+                ("tol", C.c_double), ("storage", C.c_int32), ("block", C.c_int32), ("metric", C.c_int32),
+                ("sampling", C.c_int32)]
 
 
 class AdaptiveStats(C.Structure):
@@ -66,6 +67,8 @@ def lib():
             L.orc_coordinate.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                          C.c_uint64, C.c_uint64]
             L.orc_coordinate.restype = C.c_int32
+            L.orc_coordinate_wor.argtypes = L.orc_coordinate.argtypes
+            L.orc_coordinate_wor.restype = C.c_int32
             L.orc_alpha.argtypes = [C.c_int32, C.c_double, C.c_int64, C.c_int64, C.c_double]
             L.orc_alpha.restype = C.c_double
             L.orc_exact_knn_batch.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, C.c_int32, P, P, C.c_int32]
@@ -106,6 +109,11 @@ def coordinate(seed, qid, point, s, m, mask_p=(1 << 64) - 1, mask_q=(1 << 64) - 
     return lib().orc_coordinate(seed, qid, point, s, m, mask_p, mask_q)
 
 
+def coordinate_wor(seed, qid, point, s, m, mask_p=(1 << 64) - 1, mask_q=(1 << 64) - 1):
+    """The s-th draw (s < m) of a pair sampled without replacement."""
+    return lib().orc_coordinate_wor(seed, qid, point, s, m, mask_p, mask_q)
+
+
 def alpha(form, u, n, delta, c_alpha=1.0):
     return lib().orc_alpha(BOUND[form] if isinstance(form, str) else int(form), float(c_alpha), int(u), int(n),
                            float(delta))
@@ -144,16 +152,18 @@ def exact_knn(X, Q, k, threads=0, metric="l2"):
 
 
 def make_params(k, h=None, delta=0.01, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, seed=0,
-                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32", block=1, metric="l2"):
+                qid=0, share_points=False, share_queries=False, tol=1e-5, storage="f32", block=1, metric="l2",
+                replace=True):
     """Parameters of the batched rounds; `block` = coordinates per sample
     (1: single coordinates as in the paper; g > 1: blocks of g consecutive
-    coordinates, B0 and B then count blocks)."""
+    coordinates, B0 and B then count blocks); `replace` = False draws a
+    pair's coordinates without replacement (its keyed permutation of [0, m))."""
     full = (1 << 64) - 1
     return AdaptiveParams(int(k), int(k if h is None else h), BOUND[bound] if isinstance(bound, str) else int(bound),
                           float(c_alpha), float(delta), int(B0), int(B), int(grow), int(seed), int(qid),
                           0 if share_points else full, 0 if share_queries else full, float(tol),
                           STORAGE[storage] if isinstance(storage, str) else int(storage), int(block),
-                          METRIC[metric] if isinstance(metric, str) else int(metric))
+                          METRIC[metric] if isinstance(metric, str) else int(metric), 0 if replace else 1)
 
 
 def adaptive(X, Q, params: AdaptiveParams, replay=None, want_state=True, threads=0):

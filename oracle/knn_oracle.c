@@ -78,6 +78,51 @@ int32_t orc_coordinate(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, 
     return (int32_t)(((uint64_t)word * (uint64_t)(uint32_t)m) >> 32);
 }
 
+/* MurmurHash3's 32-bit finaliser (Appleby, public domain): the round
+ * function of the permutation below. */
+static uint32_t fmix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+
+/* Eight Feistel rounds on the 2h-bit value x with round keys k[0..7]. */
+static uint32_t feistel8(uint32_t x, int h, const uint32_t k[8]) {
+    const uint32_t mask = (1u << h) - 1u;
+    uint32_t L = x >> h, R = x & mask;
+    for (int r = 0; r < 8; ++r) {
+        uint32_t nL = R;
+        uint32_t nR = L ^ (fmix32(R ^ k[r]) & mask);
+        L = nL;
+        R = nR;
+    }
+    return (L << h) | R;
+}
+
+int32_t orc_coordinate_wor(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
+                           uint64_t mask_p, uint64_t mask_q) {
+    uint64_t ctr[4] = {~(uint64_t)0, point & mask_p, qid & mask_q, 0};
+    uint64_t key[2] = {seed, 0};
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    uint32_t k[8];
+    for (int r = 0; r < 8; ++r) k[r] = (uint32_t)(out[r >> 1] >> (32 * (r & 1)));
+    int bits = 0;
+    while (((uint64_t)1 << bits) < (uint64_t)m) ++bits;  /* ceil(log2 m) */
+    int h = (bits + 1) / 2;
+    if (h < 1) h = 1;
+    /* cycle walking: s < m lies on a cycle of the permutation of [0, 4^h),
+     * so the walk meets a value below m again */
+    uint32_t x = (uint32_t)s;
+    do {
+        x = feistel8(x, h, k);
+    } while (x >= (uint32_t)m);
+    return (int32_t)x;
+}
+
 /* ----------------------------------------------------------------- alpha */
 
 double orc_alpha(int32_t form, double c_alpha, int64_t u, int64_t n, double delta) {
@@ -273,7 +318,8 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
     const int32_t k = p->k, h = p->h;
     const int64_t kh = (int64_t)k + h;
     if (k < 1 || h < 0 || n < k || m < 1 || !(p->delta > 0.0 && p->delta < 1.0) || p->B0 < 1 || p->B < 1 ||
-        p->block < 0)
+        p->block < 0 || (p->sampling != ORC_SAMPLE_WITH && p->sampling != ORC_SAMPLE_WITHOUT) ||
+        (p->sampling == ORC_SAMPLE_WITHOUT && p->block > 1))
         return 1;
     /* g coordinates per sample, M samples make the exact distance */
     const int32_t g = p->block > 1 ? p->block : 1;
@@ -352,8 +398,13 @@ static int32_t adaptive_core(const float* X, const float* G, double emax, int64_
                 Sx[i] = dist_of(metric, X + (size_t)i * (size_t)m, q, m);
             } else {
                 for (int64_t t = Tcur; t < Tn; ++t) {
-                    /* draw t picks block b: coordinates b*g .. min(b*g + g, m) - 1 */
-                    int32_t b = orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, M, p->mask_p, p->mask_q);
+                    /* draw t picks block b: coordinates b*g .. min(b*g + g, m) - 1
+                     * (without replacement g = 1 and b is the pair's t-th
+                     * coordinate of its permutation) */
+                    int32_t b = p->sampling == ORC_SAMPLE_WITHOUT
+                                    ? orc_coordinate_wor(p->seed, p->qid, (uint64_t)i, (uint64_t)t, m, p->mask_p,
+                                                         p->mask_q)
+                                    : orc_coordinate(p->seed, p->qid, (uint64_t)i, (uint64_t)t, M, p->mask_p, p->mask_q);
                     int32_t j1 = (b + 1) * g < m ? (b + 1) * g : m;
                     for (int32_t j = b * g; j < j1; ++j) Sx[i] += term_of(metric, (double)xi[j] - (double)q[j]);
                 }

@@ -33,6 +33,22 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 int32_t orc_coordinate(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
                        uint64_t mask_p, uint64_t mask_q);
 
+/* Without replacement (footnote to Section 4: a cipher on [m] makes the
+ * estimate exact after m draws). The s-th draw (0-based, s < m) of a pair is
+ * pi(s), pi a permutation of [0, m) keyed per (seed, point, query):
+ *   round keys k_0..k_7 = the eight 32-bit words (low half of each 64-bit
+ *   word first) of Philox4x64-10 at counter (2^64 - 1, point, query, 0),
+ *   key (seed, 0); a balanced Feistel network (Luby and Rackoff) of 8 rounds
+ *   on 2h bits (4 rounds leave consecutive draws visibly correlated on
+ *   small domains),
+ *   h = max(1, ceil(ceil(log2 m) / 2)): with x = (L, R), L the high h bits,
+ *   a round maps (L, R) to (R, L xor (F(k_r, R) mod 2^h)), where
+ *   F(k, R) = fmix32(R xor k), fmix32 the 32-bit finaliser of MurmurHash3;
+ *   extended to [0, m) by cycle walking (Black and Rogaway): the network is
+ *   applied again until the value is below m. */
+int32_t orc_coordinate_wor(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
+                           uint64_t mask_p, uint64_t mask_q);
+
 /* alpha(u) in normalised units ([0,1]-bounded samples). */
 double orc_alpha(int32_t form, double c_alpha, int64_t u, int64_t n, double delta);
 
@@ -58,7 +74,11 @@ typedef struct {
                            * shorter) and adds the block's sum of squared differences */
     int32_t metric;       /* ORC_METRIC_*: squared l2 (the paper's), or l1 (Section 3's generalisation):
                            * samples |x_j - q_j|, normalised by span instead of span^2 */
+    int32_t sampling;     /* ORC_SAMPLE_*: with replacement (Section 4), or without (single coordinates:
+                           * a pair's draws follow orc_coordinate_wor's permutation) */
 } orc_adaptive_params;
+
+enum { ORC_SAMPLE_WITH = 0, ORC_SAMPLE_WITHOUT = 1 };
 
 enum { ORC_METRIC_L2SQ = 0, ORC_METRIC_L1 = 1 };
 
