@@ -60,6 +60,17 @@ typedef enum {
 /* Distance of the method: squared l2 (the paper's), or l1. */
 typedef enum { KNN_METRIC_L2SQ = 0, KNN_METRIC_L1 = 1 } knn_metric;
 
+/* How a pair's coordinates are drawn: uniformly with replacement (Section 4,
+ * the default), or without replacement (the footnote to Section 4: a cipher on
+ * [m]): the pair's s-th draw is pi(s), pi a permutation of [0, m) keyed per
+ * (seed, point, query) -- an 8-round balanced Feistel network on 2h bits
+ * (4^h >= m, h >= 1) whose round keys are the eight 32-bit words of
+ * Philox4x64-10 at counter (2^64 - 1, point & mask_p, query & mask_q, 0), key
+ * (seed, 0), round function fmix32(R xor k_r) mod 2^h (MurmurHash3's
+ * finaliser), cycle-walked onto [0, m). The bounds are unchanged (Hoeffding's
+ * inequality holds for sampling without replacement). */
+typedef enum { KNN_SAMPLE_WITH = 0, KNN_SAMPLE_WITHOUT = 1 } knn_sampling;
+
 /* Options of knn_adaptive. Fill with knn_opts_default() and change fields. */
 typedef struct {
     int32_t h;          /* extra set size: returned set has at most k+h points; -1 means h = k */
@@ -87,6 +98,9 @@ typedef struct {
                          * which lie in [0, span], so bounds are d^ -/+ span alpha(T); a stored copy
                          * with element error e moves a sample by at most e (width (span + e) alpha + e);
                          * the exact cap takes sum_j |x_j - q_j| on the FP32 data */
+    int32_t sampling;   /* knn_sampling: KNN_SAMPLE_WITH (default) or KNN_SAMPLE_WITHOUT (single
+                         * coordinates, the FP32 data; not with shared-coordinate copies, block
+                         * samples, stored copies or knn_adaptive_noalloc: KNN_EINVAL) */
 } knn_opts;
 
 void knn_opts_default(knn_opts* opts);

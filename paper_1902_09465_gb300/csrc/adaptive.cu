@@ -24,6 +24,7 @@ extern "C" void knn_opts_default(knn_opts* o) {
   o->max_ctas = 0;
   o->block = 1;
   o->metric = KNN_METRIC_L2SQ;
+  o->sampling = KNN_SAMPLE_WITH;
 }
 
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {
@@ -151,6 +152,9 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   if (o.block > 1) {
     set_blocks<Blk<ElemF32>>(a, o);
     s = launch_rounds<Blk<ElemF32>>(p, a, stream);
+  } else if (o.sampling == KNN_SAMPLE_WITHOUT) {
+    set_blocks<Wor<ElemF32>>(a, o);
+    s = launch_rounds<Wor<ElemF32>>(p, a, stream);
   } else {
     set_blocks<ElemF32>(a, o);
     s = launch_rounds<ElemF32>(p, a, stream);
@@ -206,6 +210,8 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   knn_status s = validate(n, m, nq, k, delta, o);
   if (s != KNN_OK) return s;
   if (o.block > 1) return set_error("knn_adaptive_noalloc takes single coordinates (block 0 or 1)"), KNN_EINVAL;
+  if (o.sampling != KNN_SAMPLE_WITH)
+    return set_error("knn_adaptive_noalloc draws with replacement only"), KNN_EINVAL;
   if (nq == 0) return KNN_OK;
   if (!X || !Q || !out_idx || !out_count || !out_evals) {
     set_error("X, Q, out_idx, out_count and out_evals are required");

@@ -92,6 +92,7 @@ struct AdaptiveArgs {
   const int32_t* jperm; // shared-coordinate copies: column of draw t (t < m), for Perm element types
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
   unsigned long long* phase_clk;  // per-phase clock totals [16] (libraries built with phase timing; else null)
+  int32_t wor_h;        // draws without replacement: half width h of the Feistel network (4^h >= m)
 };
 
 // Phase timing (compiled in only with KNN_PHASE_TIMING): thread 0 of each CTA
@@ -135,6 +136,7 @@ struct ElemF32 {
   static constexpr bool kScaled = false;
   static constexpr bool kPerm = false;
   static constexpr bool kBlk = false;
+  static constexpr bool kWor = false;
   __device__ static __forceinline__ float load(const T* p) { return __ldg(p); }
   __device__ static __forceinline__ float conv(T v) { return v; }
 };
@@ -144,6 +146,7 @@ struct ElemBF16 {
   static constexpr bool kScaled = false;
   static constexpr bool kPerm = false;
   static constexpr bool kBlk = false;
+  static constexpr bool kWor = false;
   __device__ static __forceinline__ float conv(T v) { return __uint_as_float((uint32_t)v << 16); }
   __device__ static __forceinline__ float load(const T* p) { return conv(__ldg(p)); }
 };
@@ -153,6 +156,7 @@ struct ElemFP8 {
   static constexpr bool kScaled = true;
   static constexpr bool kPerm = false;
   static constexpr bool kBlk = false;
+  static constexpr bool kWor = false;
   __device__ static __forceinline__ float conv(T v) {
     __nv_fp8_e4m3 f;
     f.__x = v;
@@ -188,6 +192,50 @@ template <class Base>
 struct Blk : Base {
   static constexpr bool kBlk = true;
 };
+
+// Draws without replacement (single coordinates): a pair's s-th draw is the
+// s-th value of its keyed permutation of [0, m) (wor_coordinate) in place of
+// a uniform word scaled to [0, m).
+template <class Base>
+struct Wor : Base {
+  static constexpr bool kWor = true;
+};
+
+// MurmurHash3's 32-bit finaliser (Appleby, public domain): the round function
+// of the keyed permutation.
+__device__ __forceinline__ uint32_t fmix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return x;
+}
+
+// Draw s (< m) of a pair sampled without replacement (the footnote to
+// Section 4: a cipher on [m]): a balanced Feistel network of 8 rounds on 2h
+// bits (L the high h bits; a round maps (L, R) to (R, L ^ (fmix32(R ^ k_r) mod
+// 2^h))) keyed by the eight 32-bit words of the pair's Philox block k,
+// extended to [0, m) by cycle walking (apply it again until the value is
+// below m). From s < m the walk returns below m within one cycle of the
+// permutation of [0, 4^h); the walk is capped at 4^h steps all the same.
+__device__ __forceinline__ int wor_coordinate(const Philox4x64& k, uint32_t s, uint32_t m, int h) {
+  const uint32_t mask = (1u << h) - 1u;
+  const uint32_t cap = 1u << (2 * h);
+  uint32_t x = s;
+  for (uint32_t step = 0; step < cap; ++step) {
+    uint32_t L = x >> h, R = x & mask;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t nR = L ^ (fmix32(R ^ philox_word(k, r)) & mask);
+      L = R;
+      R = nR;
+    }
+    x = (L << h) | R;
+    if (x < m) return (int)x;
+  }
+  return 0;
+}
 
 // 8 consecutive elements of a shared-coordinate row (16-byte aligned blocks
 // for FP32 and BF16, 8-byte for FP8), converted to FP32.
@@ -358,7 +406,10 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
   uint64_t b;
   bool has;
   item(0, sidx, id, b, has);
-  Philox4x64 ph = has ? philox4x64_10(b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0) : Philox4x64{};
+  // (without replacement one block per pair: counter word 0 all ones, the round keys)
+  const uint64_t ctr0 = E::kWor ? ~0ull : 0ull;
+  Philox4x64 ph = has ? philox4x64_10(E::kWor ? ctr0 : b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0)
+                      : Philox4x64{};
   float part = 0.0f;
   for (int t = 0; t < nitems; ++t) {
     // issue the current item's loads
@@ -371,7 +422,10 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
     for (int w = 0; w < 8; ++w) {
       const int64_t s = s0 + w;
       ok[w] = has && (s >= T) && (s < Tn);
-      jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+      if constexpr (E::kWor)
+        jj[w] = ok[w] ? wor_coordinate(ph, (uint32_t)s, (uint32_t)m, a.wor_h) : 0;  // s < Tn < m
+      else
+        jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
       xv[w] = ok[w] ? E::load(xr + jj[w]) : 0.0f;
     }
     const float sc = (E::kScaled && has) ? __ldg(a.gscale + id) : 1.0f;
@@ -380,7 +434,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
     // the next item's Philox while the loads are in flight
     if (t + 1 < nitems) {
       item(t + 1, sidx, id, b, has);
-      if (has) ph = philox4x64_10(b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0);
+      if (has) ph = philox4x64_10(E::kWor ? ctr0 : b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0);
     }
     // consume
     if (cur_has) {
@@ -1068,13 +1122,14 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
       float part = 0.0f;
       if (pi < np && gl < nblk) {
         const uint64_t id = (uint64_t)(p0 + pi);
-        const Philox4x64 ph = philox4x64_10((uint64_t)gl, id & a.mask_p, qfield, 0, a.seed, 0);
+        const Philox4x64 ph = philox4x64_10(E::kWor ? ~0ull : (uint64_t)gl, id & a.mask_p, qfield, 0, a.seed, 0);
         const float* xr = rows + (size_t)pi * m;
         if constexpr (!E::kBlk) {
 #pragma unroll
           for (int w = 0; w < 8; ++w) {
-            if (gl * 8 + w < a.B0) {
-              const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+            if (gl * 8 + w < a.B0) {  // B0 < m: the draw index is below m
+              const int j = E::kWor ? wor_coordinate(ph, (uint32_t)(gl * 8 + w), (uint32_t)m, a.wor_h)
+                                    : (int)__umulhi(philox_word(ph, w), (uint32_t)m);
               const float d = xr[j] - __ldg(qr + j);
               part = add_term<L1>(d, part);
             }
@@ -1399,6 +1454,9 @@ static inline void set_blocks(AdaptiveArgs& a, const knn_opts& o) {
   a.g = g;
   a.Mb = (a.m + g - 1) / g;
   a.gvec = (g > 1 && (size_t)g * elem == 32 && ((size_t)a.m * elem) % 16 == 0 && ((uintptr_t)a.G & 15) == 0) ? 1 : 0;
+  int bits = 0;  // ceil(log2 m)
+  while ((1 << bits) < a.m) ++bits;
+  a.wor_h = E::kWor ? std::max(1, (bits + 1) / 2) : 0;
 }
 
 // Queries per chunk: as many as the buffer holds, but never fewer than the
@@ -1425,6 +1483,10 @@ static knn_status validate(int64_t n, int32_t m, int32_t nq, int32_t k, double d
   if (o.grow != 0 && o.grow != 1) return set_error("grow must be 0 or 1"), KNN_EINVAL;
   if (o.block < 0 || o.block > 64) return set_error("block must be in [0, 64]"), KNN_EINVAL;
   if (o.metric != KNN_METRIC_L2SQ && o.metric != KNN_METRIC_L1) return set_error("unknown metric"), KNN_EINVAL;
+  if (o.sampling != KNN_SAMPLE_WITH && o.sampling != KNN_SAMPLE_WITHOUT)
+    return set_error("unknown sampling"), KNN_EINVAL;
+  if (o.sampling == KNN_SAMPLE_WITHOUT && o.block > 1)
+    return set_error("sampling without replacement takes single coordinates (block 0 or 1)"), KNN_EINVAL;
   return KNN_OK;
 }
 

@@ -12,6 +12,7 @@ namespace knn {
 extern template KNN_DS_LAUNCH_DECL(ElemF32);
 extern template KNN_DS_LAUNCH_DECL(Perm<ElemF32>);
 extern template KNN_DS_LAUNCH_DECL(Blk<ElemF32>);
+extern template KNN_DS_LAUNCH_DECL(Wor<ElemF32>);
 extern template KNN_DS_LAUNCH_DECL(ElemBF16);
 extern template KNN_DS_LAUNCH_DECL(Perm<ElemBF16>);
 extern template KNN_DS_LAUNCH_DECL(Blk<ElemBF16>);
@@ -192,8 +193,8 @@ static knn_status dispatch_ds(const knn_dataset* ds, int32_t storage, const floa
                               int64_t* out_evals, int32_t* out_rounds, int32_t* log_code, float* log_S,
                               void* workspace, size_t workspace_bytes, cudaStream_t stream, const MixedBatch* mix) {
   // (shared-coordinate copies hold single coordinates: block samples draw per pair)
-  const bool shared = o.mask_p == 0 && o.mask_q == 0 && o.block <= 1 && ((ds->share_ready >> storage) & 1) &&
-                      ds->share_seed == seed;
+  const bool shared = o.mask_p == 0 && o.mask_q == 0 && o.block <= 1 && o.sampling == KNN_SAMPLE_WITH &&
+                      ((ds->share_ready >> storage) & 1) && ds->share_seed == seed;
 #define KNN_DS_LAUNCH(E)                                                                                        \
   return adaptive_ds_launch<E>(ds, Q, nq, k, delta, seed, o, out_idx, out_count, out_evals, out_rounds, log_code, \
                                log_S, workspace, workspace_bytes, stream, mix)
@@ -201,6 +202,11 @@ static knn_status dispatch_ds(const knn_dataset* ds, int32_t storage, const floa
     if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(Perm<ElemBF16>);
     if (storage == KNN_STORE_FP8) KNN_DS_LAUNCH(Perm<ElemFP8>);
     KNN_DS_LAUNCH(Perm<ElemF32>);
+  }
+  if (o.sampling == KNN_SAMPLE_WITHOUT) {
+    if (storage != KNN_STORE_F32)
+      return set_error("sampling without replacement gathers from the FP32 data (storage F32)"), KNN_EINVAL;
+    KNN_DS_LAUNCH(Wor<ElemF32>);
   }
   if (o.block > 1) {
     if (storage == KNN_STORE_BF16) KNN_DS_LAUNCH(Blk<ElemBF16>);

@@ -23,13 +23,13 @@ def run_gpu(X, Q, k, delta, seed, **opts):
 
 
 def check(X, Q, k, delta=0.01, seed=0, queries=None, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0,
-          qid_base=0, share_points=False, share_queries=False, gpu=None, block=1, threads=0):
+          qid_base=0, share_points=False, share_queries=False, gpu=None, block=1, threads=0, replace=True):
     """Runs the GPU (unless `gpu` holds a previous result) and replays the
     chosen queries in the oracle. Returns a summary dict."""
     if gpu is None:
         gpu = run_gpu(X, Q, k, delta, seed, h=h, bound=bound, c_alpha=c_alpha, B0=B0, B=B, grow=grow,
                       qid_base=qid_base, share_points=share_points, share_queries=share_queries, block=block,
-                      threads=threads)
+                      threads=threads, replace=replace)
     nq, n = Q.shape[0], X.shape[0]
     hh = k if h is None else h
     kh = k + hh
@@ -38,7 +38,7 @@ def check(X, Q, k, delta=0.01, seed=0, queries=None, h=None, bound="footnote", c
     for q in queries:
         p = oracle.make_params(k, h=hh, delta=delta, bound=bound, c_alpha=c_alpha, B0=B0, B=B, grow=grow, seed=seed,
                                qid=qid_base + q, share_points=share_points, share_queries=share_queries,
-                               tol=TOL_DECISION, block=block)
+                               tol=TOL_DECISION, block=block, replace=replace)
         o = oracle.adaptive(X, Q[q:q + 1], p, replay=gpu["code"][q:q + 1])
         st = o["stats"][0]
         assert st["mismatch"] == 0, (q, st)

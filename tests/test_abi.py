@@ -69,11 +69,20 @@ def test_invalid_arguments_are_rejected_on_the_host(lib_path):
                             None, None, 0, None)
         assert rc == 1, (field, value)
         assert field.split("_")[0] in L.knn_last_error().decode() or L.knn_last_error().decode()
+    # sampling: an unknown mode, and without replacement over block samples
+    for fields in ({"sampling": 2}, {"sampling": -1}, {"sampling": 1, "block": 8}):
+        bad = knn.Opts()
+        L.knn_opts_default(ctypes.byref(bad))
+        for f, v in fields.items():
+            setattr(bad, f, v)
+        rc = L.knn_adaptive(None, 100, 8, None, 1, 2, 0.1, 0, ctypes.byref(bad), None, None, None, None, None,
+                            None, None, 0, None)
+        assert rc == 1 and "sampling" in L.knn_last_error().decode(), fields
     rc = L.knn_rerank_metric(None, 10, 4, None, 1, None, 4, 1, 3, None, None, None)
     assert rc == 1 and "metric" in L.knn_last_error().decode()
     o2 = knn.Opts()
     L.knn_opts_default(ctypes.byref(o2))
-    assert o2.block == 1 and o2.metric == 0
+    assert o2.block == 1 and o2.metric == 0 and o2.sampling == 0
 
 
 def test_phase_clocks_only_in_the_timing_build(lib_path):

@@ -26,7 +26,8 @@ def _args(**kw):
     return a
 
 
-def test_phase_shares_and_gather_rate():
+def test_phase_shares_and_gather_rate(monkeypatch):
+    monkeypatch.setattr(bench, "kernel_sources_sha1", lambda: bench.TRAFFIC_CAPTURE["sha1"])
     cfg = bench.TRAFFIC_CAPTURE["config"]
     opts = {key: cfg[key] for key in ("c_alpha", "B0", "B", "grow", "threads")}
     w = dict(bench.WORKLOAD, nq=cfg["nq"])
@@ -42,8 +43,9 @@ def test_phase_shares_and_gather_rate():
 
 
 @pytest.mark.parametrize("change", [dict(opt="B0", val=16), dict(arg="storage", val="bf16"), dict(arg="share", val=True),
-                                    dict(arg="block", val=8), dict(w="nq", val=64)])
-def test_gather_rate_only_for_the_captured_configuration(change):
+                                    dict(arg="block", val=8), dict(w="nq", val=64), dict(sha="0" * 40)])
+def test_gather_rate_only_for_the_captured_configuration(change, monkeypatch):
+    monkeypatch.setattr(bench, "kernel_sources_sha1", lambda: bench.TRAFFIC_CAPTURE["sha1"])
     cfg = bench.TRAFFIC_CAPTURE["config"]
     opts = {key: cfg[key] for key in ("c_alpha", "B0", "B", "grow", "threads")}
     w = dict(bench.WORKLOAD, nq=cfg["nq"])
@@ -52,8 +54,10 @@ def test_gather_rate_only_for_the_captured_configuration(change):
         opts[change["opt"]] = change["val"]
     elif "arg" in change:
         setattr(args, change["arg"], change["val"])
-    else:
+    elif "w" in change:
         w[change["w"]] = change["val"]
+    else:  # kernel sources changed since the capture
+        monkeypatch.setattr(bench, "kernel_sources_sha1", lambda: change["sha"])
     assert "gather_phase_dram" not in bench.phase_report(_clk(6, 2, 1), opts, args, w)
 
 
