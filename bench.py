@@ -401,6 +401,39 @@ def run_ours(args, rank, world, local_rank):
             "tuned": b, "coord_evals_fraction": round(ev_s / (nq * n * m), 6),
             "alg_gbs_step": round(elem * ev_s / (ms_s / 1e3) / 1e9, 2)}
 
+    # ---- draws without replacement (each pair's keyed permutation of [0, m)), FP32, per pair
+    # (a variant report: an error here is recorded in place of the numbers, the line stays;
+    # one GPU only, so that no rank can wait in a collective that another left)
+    try:
+        if world > 1:
+            raise RuntimeError("reported by single-GPU runs only")
+        WOR = {"replace": False}
+        t = runtime.autotune(ds, Hd, k, w["delta"], storage="f32", target=RECALL_TARGET, margin=0.0005,
+                             c_grid=[args.c_alpha] if args.c_alpha else C_GRID, use_cache=False, extra=WOR,
+                             cache=os.path.join(tempfile.gettempdir(), f"knn_bench_tune_wor_{os.getpid()}.json"))
+        b = t["best"]
+        step = runtime.GraphStep(ds, nq, k, w["delta"], 0, storage="f32", qid_base=qid_base,
+                                 **dict(opts_of(b), **WOR))
+        for _ in range(2):
+            step.run(Qd)
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        vsteps = max(2, min(args.steps, 5))
+        for _ in range(vsteps):
+            res_s, ri_s, rd_s = step.run(Qd)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = max_over_ranks(v0.elapsed_time(v1) / vsteps)
+        ev_s = int(res_s["evals"].sum().item())
+        without_replacement = {
+            "queries_per_s": round(world * nq / (ms_s / 1e3), 3), "ms_per_step": round(ms_s, 4),
+            "recall": round(recall_of(ri_s.cpu().numpy(), rd_s.cpu().numpy(), ti_np, td_np), 6),
+            "tuned": b, "coord_evals_fraction": round(ev_s / (nq * n * m), 6)}
+    except Exception as exc:  # noqa: BLE001 -- reported, not hidden
+        without_replacement = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+
     # ---- end to end through the public API with host buffers
     Qh = torch.from_numpy(Q).pin_memory()
     ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
@@ -447,6 +480,7 @@ def run_ours(args, rank, world, local_rank):
         "storage_variants": variants,
         "shared_coordinates": shared,
         "block_samples": blocks,
+        "without_replacement": without_replacement,
         "exact_baseline": {"queries_per_s": round(world * nq / (exact_ms / 1e3), 3), "ms_per_batch": round(exact_ms, 4),
                            "method": "tcgen05 BF16x3 screen GEMM + select + FP64 rerank (exact)",
                            "agrees_with_simt_path": exact_agree,
