@@ -24,8 +24,9 @@
 // per-round scalar, and the per-point state is (id, S, Kahan term).
 //
 // Variants, each a template argument: the element type wraps the copy
-// for shared coordinates (Perm: row prefixes of a column-permuted copy) or
-// block samples (Blk: one of ceil(m/g) blocks of g coordinates per draw); a
+// for shared coordinates (Perm: row prefixes of a column-permuted copy),
+// block samples (Blk: one of ceil(m/g) blocks of g coordinates per draw) or
+// draws without replacement (Wor: each pair's keyed permutation of [0, m)); a
 // bool selects the l1 distance (|x - q| terms, span-scaled widths). Round 0
 // of a dataset call comes from a point-major pass (round0_kernel for per-pair
 // draws, round0_shared_kernel for shared coordinates) that writes the
