@@ -519,6 +519,32 @@ def oracle_schedule(args, cfg=None):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu; the machine type if it has none)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
+def oracle_single_thread(X, Q, p, budget_s=3.0):
+    """The oracle on one core over the first queries, within a small time budget."""
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done < Q.shape[0]:
+        oracle.adaptive(X, Q[done: done + 1], p, want_state=False, threads=1)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 4), "unit": "queries/s", "cores": 1,
+            "sample": f"{done} queries (first ones), {dt:.1f} s"}
+
+
 def cpu_baseline(args, budget_s=15.0, X=None, Q=None, cfg=None):
     import oracle
     w = WORKLOAD
@@ -535,7 +561,8 @@ def cpu_baseline(args, budget_s=15.0, X=None, Q=None, cfg=None):
     dt = time.perf_counter() - t0
     return {"value": round(done / dt, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": f"{done} of {Q.shape[0]} queries (first ones), C_alpha={sch['c_alpha']}, "
-                      f"B0={sch['B0']} B={sch['B']} grow={sch['grow']}, FP64, OpenMP over queries, {dt:.1f} s"}
+                      f"B0={sch['B0']} B={sch['B']} grow={sch['grow']}, FP64, OpenMP over queries, {dt:.1f} s",
+            "cpu_model": cpu_model(), "single_thread": oracle_single_thread(X, Q, p)}
 
 
 def run_reference(args, rank, world):
@@ -563,7 +590,8 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], **sch, "sample_per_step": per_step},
             "cpu_baseline": {"value": round(v, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} queries per step of the {w['nq']}-query batch"},
+                             "sample": f"{per_step} queries per step of the {w['nq']}-query batch",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": round(v, 4), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
