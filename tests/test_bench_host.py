@@ -84,3 +84,13 @@ def test_oracle_schedule_follows_the_gpu_arm():
     assert bench.oracle_schedule(_args()) == {key: rec[key] for key in ("c_alpha", "B0", "B", "grow")}
     assert bench.oracle_schedule(_args(B0=4, cpu_c_alpha=1e-2))["B0"] == 4
     assert bench.oracle_schedule(_args(B0=4, cpu_c_alpha=1e-2))["c_alpha"] == 1e-2
+
+
+def test_cpu_baseline_reports_model_and_single_core_rate():
+    from paper_1902_09465_gb300 import synth
+    X, Q = synth.pixel_mixture(2000, 64, 8, seed=1)
+    r = bench.cpu_baseline(_args(), budget_s=0.5, X=X, Q=Q)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert isinstance(r["cpu_model"], str) and r["cpu_model"]
+    st = r["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and "queries" in st["sample"]
