@@ -57,3 +57,39 @@ def test_heaps_contain_the_knn_and_scale():
     ti, _ = oracle.exact_knn(X, Q, 5)
     assert set(ti[0]) <= set(idx.tolist())
     assert ev < 0.2 * 20000 * 128
+
+
+# ------------------------------------------------ closed-form limits of Algorithm 1
+
+@pytest.mark.parametrize("heaps", [False, True])
+@pytest.mark.parametrize("n,m,k", [(40, 12, 3), (25, 7, 1), (30, 1, 4)])
+def test_wide_bounds_compute_every_distance(heaps, n, m, k):
+    """With h = 0 and a huge C_alpha no sampled bound separates anything, so
+    Algorithm 1 stops only once every point is exact: each point costs its
+    initial draw, m - 1 more and the m of its exact distance (2m; a point of
+    m = 1 is exact from its only draw, 1), and the result is the exact k
+    nearest by (distance, index)."""
+    X, Q, _ = synth.gaussian_planted(n, m, k, seed=n + m)
+    p = oracle.make_params(k, h=0, delta=0.05, bound="exp", c_alpha=1e12, seed=2)
+    idx, evals, iters = oracle.sequential(X, Q[0], p, heaps=heaps)
+    ti, _ = oracle.exact_knn(X, Q[0:1], k)
+    np.testing.assert_array_equal(idx, ti[0])
+    assert evals == (n if m == 1 else 2 * m * n)
+
+
+@pytest.mark.parametrize("heaps", [False, True])
+def test_vanishing_bounds_stop_before_the_first_iteration(heaps):
+    """With C_alpha -> 0 every bound is its estimate, and the estimates are in
+    order, so the termination test holds at once: no iteration, one draw per
+    point, and the k + h smallest single-draw estimates by (estimate, index)
+    (the draws are orc_coordinate's, pinned to numpy's Philox)."""
+    n, m, k, h = 60, 50, 4, 3
+    X, Q, _ = synth.gaussian_planted(n, m, k, seed=11)
+    q = Q[0]
+    p = oracle.make_params(k, h=h, delta=0.05, bound="exp", c_alpha=1e-300, seed=5, qid=7)
+    idx, evals, iters = oracle.sequential(X, q, p, heaps=heaps)
+    assert iters == 0 and evals == n
+    est = np.array([(float(X[i, j]) - float(q[j])) ** 2
+                    for i, j in ((i, oracle.coordinate(5, 7, i, 0, m)) for i in range(n))])
+    want = np.lexsort((np.arange(n), est))[: k + h]
+    np.testing.assert_array_equal(idx, want)
