@@ -124,7 +124,11 @@ int32_t orc_adaptive_batch(const float* X, int64_t n, int32_t m, const float* Q,
                            orc_adaptive_stats* st, int32_t threads);
 
 /* Algorithm 1 as printed (two arms per iteration, LUCB indices q1, b2),
- * with O(n) scans in place of the seven heaps. out_idx[k+h]. */
+ * with O(n) scans in place of the seven heaps. out_idx[k+h]. Pinned at its
+ * two closed-form limits (wide bounds: every distance exact; vanishing
+ * bounds: no iteration) and by Theorem 1's containment; the iteration
+ * counts in between are fixed by nothing in the paper (parity unpinned
+ * there). */
 int32_t orc_sequential(const float* X, int64_t n, int32_t m, const float* q,
                        const orc_adaptive_params* p, int64_t max_iter,
                        int64_t* out_idx, int64_t* out_evals, int64_t* out_iters);
