@@ -43,3 +43,12 @@ def test_exact_engine_allows_the_full_candidate_limit():
     s.submit(serve.Request(rid=0, dataset=0, Q=torch.zeros(1, 16), k=1000))
     with pytest.raises(ValueError):
         s.submit(serve.Request(rid=1, dataset=0, Q=torch.zeros(1, 16), k=1001))
+
+
+def test_dataset_options_reach_the_launch():
+    ds = types.SimpleNamespace(n=1000, m=16)
+    s = serve.Server([ds, ds], [serve.DatasetConfig(c_alpha=3e-4, B0=16, threads=1024),
+                                serve.DatasetConfig(replace=False)], slots=0)
+    o0, o1 = s._opts(0), s._opts(1)
+    assert o0["c_alpha"] == 3e-4 and o0["B0"] == 16 and o0["threads"] == 1024 and "replace" not in o0
+    assert o1["replace"] is False and "share_points" not in o1
