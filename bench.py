@@ -17,8 +17,17 @@ Under torchrun (N > 1) every rank runs its own batch of queries against its
 own copy of the dataset (independent replicas, weak scaling); the step time
 is the maximum over ranks.
 
+The same line reports the variants beside the headline: stored BF16 / FP8
+copies, shared coordinates, 32-byte block samples and draws without
+replacement, each autotuned the same way; the exact method with both screens;
+the roofline of the adaptive call; the path end to end from pinned host
+buffers; and the oracle on this host's cores.
+
 --impl reference times the CPU oracle (double precision, OpenMP over
 queries) on a bounded sample of the same workload on this host's cores.
+Other modes: --sweep (gap-ratio precision sweep), --figure2 (Section 5's
+C_alpha sweep), --serve (the request loop), --profile-step (the timed step
+alone, for profilers; --phases adds the phase-timing build's clock shares).
 """
 
 from __future__ import annotations
