@@ -103,3 +103,31 @@ def test_l1_width_scales_with_span(w, decided):
         assert kind[0] == oracle.ACCEPTED and np.all(kind[1:] == oracle.ELIMINATED)
     else:
         assert np.all((r["code"][0][:3] >> 2) >= 1)
+
+
+@pytest.mark.parametrize("slack,decided", [(1.5, True), (0.5, False)])
+def test_l1_copy_term_is_the_element_error(slack, decided):
+    """Under l1 a stored copy moves a sample |x - q| by at most e, so the
+    width is (span + e) alpha + e. Query and point 0 at 0, points 1 and 2 at
+    257 (BF16 copy 256: e = 1), point 3 at 4096 (span 4096): estimates 0, 256,
+    256, 4096; round 0 decides everything iff the width is below 128. With
+    (span + e) alpha = 128 - slack the width is 128.5 - slack: decided for
+    slack 1.5, not for 0.5 (a dropped e would decide both; the l2 term
+    e (2 span + e) = 8193 would decide neither)."""
+    m, u, n, delta, e, span = 32, 2, 4, 0.01, 1.0, 4096.0
+    X = np.zeros((n, m), dtype=np.float32)
+    X[1:3] = 257.0
+    X[3] = span
+    q = np.zeros((1, m), dtype=np.float32)
+    _, _, emax = oracle.quantize(X, "bf16")
+    assert emax == e
+    a = (128.0 - slack) / (span + e)
+    c = a * a * u / np.log(1.0 + (1.0 + np.log(u)) * n / delta)  # alpha(u) = a, Section 5 form
+    r = oracle.adaptive(X, q, oracle.make_params(1, h=0, delta=delta, bound="exp", c_alpha=c, B0=u, B=u,
+                                                 metric="l1", storage="bf16"))
+    kind = r["code"][0] & 3
+    if decided:
+        assert r["stats"][0]["rounds"] == 1 and list(r["idx"][0]) == [0]
+        assert kind[0] == oracle.ACCEPTED and np.all(kind[1:] == oracle.ELIMINATED)
+    else:
+        assert np.all((r["code"][0][:3] >> 2) >= 1)
