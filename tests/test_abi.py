@@ -78,6 +78,16 @@ def test_invalid_arguments_are_rejected_on_the_host(lib_path):
         rc = L.knn_adaptive(None, 100, 8, None, 1, 2, 0.1, 0, ctypes.byref(bad), None, None, None, None, None,
                             None, None, 0, None)
         assert rc == 1 and "sampling" in L.knn_last_error().decode(), fields
+    # the no-alloc entry draws with replacement only (refused before any device work)
+    wor = knn.Opts()
+    L.knn_opts_default(ctypes.byref(wor))
+    wor.sampling = 1
+    fn = L.knn_adaptive_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                   ctypes.c_double, ctypes.c_uint64, ctypes.POINTER(knn.Opts)] + [ctypes.c_void_p] * 7
+    rc = fn(None, 100, 8, None, 1, 2, 0.1, 0, ctypes.byref(wor), None, None, None, None, None, None, None)
+    assert rc == 1 and "replacement" in L.knn_last_error().decode()
     rc = L.knn_rerank_metric(None, 10, 4, None, 1, None, 4, 1, 3, None, None, None)
     assert rc == 1 and "metric" in L.knn_last_error().decode()
     o2 = knn.Opts()
