@@ -85,6 +85,63 @@ def test_alpha_exp_special_value():
         assert oracle.alpha("exp", 1, 1, d, c_alpha=c) == pytest.approx(math.sqrt(5 * c), rel=1e-12)
 
 
+# alpha at u > 1. Each case fixes delta so the delta-dependent part takes a
+# known constant, then compares with decimal values worked out by hand from
+# the bound's definition (natural logarithms throughout), so the u-dependent
+# terms are pinned: a wrong factor (3 for 1.5), a base-2 logarithm, a dropped
+# "1 +", u in place of 1/u, or delta in place of delta' = delta / n fails.
+# n = 10 so that the division by n is exercised too.
+
+@pytest.mark.parametrize("u,expected", [
+    # delta' = exp(-e): log(1/delta') + 3 log log(1/delta') = e + 3 = 5.718281828...
+    # u = 2:     ln 2 = 0.693147181, ln(1.693147181) = 0.526589034, x 1.5 = 0.789883551,
+    #            beta = 6.508165380, alpha = sqrt(2 beta / 2) = 2.551110617
+    (2, 2.551110617),
+    # u = 10:    ln 10 = 2.302585093, ln(3.302585093) = 1.194705523, x 1.5 = 1.792058285,
+    #            beta = 7.510340113, alpha = sqrt(2 beta / 10) = 1.225588847
+    (10, 1.225588847),
+    # u = 12288: ln 12288 = ln 3 + 12 ln 2 = 9.416378455, ln(10.416378455) = 2.343379419,
+    #            x 1.5 = 3.515069128, beta = 9.233350957, alpha = sqrt(2 beta / 12288) = 0.03876627463
+    (12288, 0.03876627463),
+])
+def test_alpha_footnote_values_above_one(u, expected):
+    n = 10
+    d = n * math.exp(-math.e)          # delta' = delta / n = exp(-e)
+    assert oracle.alpha("footnote", u, n, d) == pytest.approx(expected, rel=2e-9)
+
+
+@pytest.mark.parametrize("u,expected", [
+    # delta' = 125 ln(1.12) / e^10, so beta(u) = 20 + 2 ln(ln(1.12 u) / ln(1.12)); ln 1.12 = 0.1133286853
+    # u = 2:     ln 2.24 = 0.8064758659, ratio 7.116255374, ln = 1.962381656, beta = 23.92476331,
+    #            alpha = sqrt(2 beta / 2) = 4.891294646
+    (2, 4.891294646),
+    # u = 10:    ln 11.2 = 2.415913778, ratio 21.31776056, ln = 3.059540555, beta = 26.11908111,
+    #            alpha = sqrt(2 beta / 10) = 2.285566937
+    (10, 2.285566937),
+    # u = 12288: ln 13762.56 = 9.529707141, ratio 84.08909990, ln = 4.431876950, beta = 28.86375390,
+    #            alpha = sqrt(2 beta / 12288) = 0.06854105785
+    (12288, 0.06854105785),
+])
+def test_alpha_lemma_values_above_one(u, expected):
+    n = 10
+    d = n * 125 * math.log(1.12) / math.exp(10)
+    assert oracle.alpha("lemma", u, n, d) == pytest.approx(expected, rel=2e-9)
+
+
+@pytest.mark.parametrize("u,c,expected", [
+    # delta = n (1 + ln u) / (e^5 - 1) makes (1 + ln u) n / delta = e^5 - 1, so the
+    # logarithm is exactly 5 and alpha(u) = sqrt(5 C_alpha / u).
+    (2, 1.0, 1.581138830),        # sqrt(2.5)
+    (2, 1e-3, 0.05),              # sqrt(0.0025)
+    (10, 1.0, 0.7071067812),      # sqrt(0.5)
+    (12288, 1.0, 0.02017178826),  # sqrt(5 / 12288)
+])
+def test_alpha_exp_values_above_one(u, c, expected):
+    n = 10
+    d = n * (1.0 + math.log(u)) / (math.exp(5) - 1)
+    assert oracle.alpha("exp", u, n, d, c_alpha=c) == pytest.approx(expected, rel=2e-9)
+
+
 @pytest.mark.parametrize("form", ["footnote", "lemma", "exp"])
 def test_alpha_decreasing_and_lil_rate(form):
     a = np.array([oracle.alpha(form, u, 1000, 0.01) for u in range(1, 5000)])
