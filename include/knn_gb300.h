@@ -117,7 +117,7 @@ size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, 
  *   (qid_base+q) & mask_q, 0), 32-bit word s mod 8 scaled by floor(w m / 2^32),
  *   s = 0,1,2,... the point's sample number); sums (X[i,j] - Q[q,j])^2 into a
  *   running FP32 sum S_i (Kahan-compensated), or computes the exact distance
- *   once T + B_r >= m ("If T = m, compute exactly", Algorithm 1);
+ *   once T + B_r >= m (Algorithm 1's exact-evaluation step at T = m);
  *   with span = max(X, Q[q]) - min(X, Q[q]) (the normalisation of Section 3)
  *   forms UCB/LCB = S_i/T -/+ span^2 alpha(T);
  *   tau_U = k-th smallest UCB over non-eliminated points, tau_L = min((k+1)-th
@@ -165,7 +165,11 @@ knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const float* Q, in
  *   lists exceed the array (n above roughly 2.7 million).
  * - The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   before any stream capture. The address is cached with the id of the
+ *   CUDA context it was found in, and looked up again when the current
+ *   context differs (after cudaDeviceReset or a recreated primary context
+ *   the module loads again and the array may move); after such a reset, make
+ *   one call again before capturing.
  * - Every call shares the one array and starts by resetting the parts that
  *   must start fresh. Calls whose work overlaps on the GPU (on different
  *   streams or from different threads without ordering) race on the array

@@ -173,28 +173,13 @@ namespace knn {
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // 64 MiB
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[64] = {};  // device address of the array, per device
+static SymbolSlot g_noalloc_slots[64];  // device address of the array, per device and context
 
 // In host code the array's name is only a host-side stand-in; the device
-// address is looked up once per device, with that device current.
+// address is looked up with the device current, once per CUDA context.
 static knn_status noalloc_address(void** out) {
-  int dev = 0;
-  knn_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
-  if (s != KNN_OK) return s;
-  if (dev < 0 || dev >= 64) {
-    set_error("device ordinal out of range");
-    return KNN_EUNSUPPORTED;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    s = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(no-alloc scratch)");
-    if (s != KNN_OK) return s;
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
-  return KNN_OK;
+  return symbol_address(reinterpret_cast<const void*>(&g_noalloc_scratch), g_noalloc_slots, out,
+                        "cudaGetSymbolAddress(no-alloc scratch)");
 }
 
 }  // namespace knn

@@ -1,5 +1,7 @@
 // api.cu -- host runtime of the C ABI: error messages, device queries and
 // stream-ordered workspaces.
+#include <cuda.h>
+
 #include <mutex>
 #include <string>
 
@@ -78,9 +80,46 @@ void Workspace::release() {
 // Status word per device (see knn_device_status).
 static __device__ int g_device_status;
 
-knn_status device_status_ptr(int** out) {
+// Unique id of the calling thread's current context (cuCtxGetId, resolved
+// through the runtime so the library needs no link-time driver dependency).
+static knn_status current_context_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static std::once_flag once;
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) {
+    set_error("cuCtxGetCurrent / cuCtxGetId unavailable from the driver");
+    return KNN_ECUDA;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return set_error("cuCtxGetCurrent failed"), KNN_ECUDA;
+  if (!ctx) {
+    // no context current yet: cudaSetDevice initialises the device's primary
+    // context and makes it current
+    int dev = 0;
+    knn_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (s == KNN_OK) s = cuda_check(cudaSetDevice(dev), "cudaSetDevice");
+    if (s != KNN_OK) return s;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return set_error("no current CUDA context"), KNN_ECUDA;
+  }
+  if (get_id(ctx, id) != CUDA_SUCCESS) return set_error("cuCtxGetId failed"), KNN_ECUDA;
+  return KNN_OK;
+}
+
+knn_status symbol_address(const void* symbol, SymbolSlot (&slots)[64], void** out, const char* what) {
   static std::mutex mu;
-  static int* addr[64] = {};
   int dev = 0;
   knn_status s = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   if (s != KNN_OK) return s;
@@ -88,14 +127,28 @@ knn_status device_status_ptr(int** out) {
     set_error("device ordinal out of range");
     return KNN_EUNSUPPORTED;
   }
+  unsigned long long ctx = 0;
+  s = current_context_id(&ctx);
+  if (s != KNN_OK) return s;
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  if (!slots[dev].addr || slots[dev].ctx != ctx) {
     void* p = nullptr;
-    s = cuda_check(cudaGetSymbolAddress(&p, g_device_status), "cudaGetSymbolAddress(status)");
+    s = cuda_check(cudaGetSymbolAddress(&p, symbol), what);
     if (s != KNN_OK) return s;
-    addr[dev] = static_cast<int*>(p);
+    slots[dev].addr = p;
+    slots[dev].ctx = ctx;
   }
-  *out = addr[dev];
+  *out = slots[dev].addr;
+  return KNN_OK;
+}
+
+knn_status device_status_ptr(int** out) {
+  static SymbolSlot slots[64];
+  void* p = nullptr;
+  knn_status s = symbol_address(reinterpret_cast<const void*>(&g_device_status), slots, &p,
+                                "cudaGetSymbolAddress(status)");
+  if (s != KNN_OK) return s;
+  *out = static_cast<int*>(p);
   return KNN_OK;
 }
 

@@ -50,6 +50,19 @@ struct Workspace {
   void release();
 };
 
+// Device address of a __device__ variable of this library (`symbol` is the
+// host-side stand-in the variable's name gives in host code) in the current
+// CUDA context. The address is cached per device together with the context's
+// unique id, and looked up again when that context changed (after a
+// cudaDeviceReset, or a primary context released and created again, the
+// module loads anew and the variable may move). The first call in a context
+// does the lookup; later calls only compare ids.
+struct SymbolSlot {
+  unsigned long long ctx = 0;
+  void* addr = nullptr;
+};
+knn_status symbol_address(const void* symbol, SymbolSlot (&slots)[64], void** out, const char* what);
+
 // Library status word of the current device: kernels that give up a bounded
 // wait record a code here (read and cleared by knn_device_status).
 knn_status device_status_ptr(int** out);

@@ -87,3 +87,20 @@ def test_noalloc_rejects_sizes_beyond_the_fixed_scratch():
     rc, _ = _call(f, Xd, Qd, 1, 0.01, 0, knn.make_opts(1), False)
     assert rc == 1
     assert "scratch" in knn.lib().knn_last_error().decode()
+
+
+@pytest.mark.parametrize("threads,max_ctas", [(1024, 0), (256, 7), (512, 3)])
+def test_noalloc_matches_for_each_cta_layout(threads, max_ctas):
+    """Per-CTA slots of the fixed array follow the launch's grid: 1,024-thread
+    CTAs with a grid the array shrinks, and grids capped by max_ctas."""
+    f = _noalloc()
+    k, delta, seed = 10, 0.01, 9
+    X, Q = synth.pixel_mixture(60000, 200, 24, seed=5)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    opt = dict(bound="exp", c_alpha=1e-3, B0=8, B=8, grow=1, threads=threads, max_ctas=max_ctas)
+    ref = knn.adaptive(Xd, Qd, k, delta, seed, **opt)
+    rc, got = _call(f, Xd, Qd, k, delta, seed, knn.make_opts(k, **opt), False)
+    assert rc == 0, knn.lib().knn_last_error().decode()
+    torch.cuda.synchronize()
+    for key in ref:
+        assert torch.equal(got[key], ref[key]), key
