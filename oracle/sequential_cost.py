@@ -3,9 +3,10 @@ version), both on the CPU oracle: the fraction of the naive method's
 coordinate evaluations (n m) each spends, and whether the k nearest are
 returned, on the same seeded inputs and the same bound (Section 5's form).
 
-    python tests/sequential_cost.py
+    python oracle/sequential_cost.py
 
-Test infrastructure: it runs the oracle only (inputs from the seeded generators)."""
+Test infrastructure like the rest of this folder: it runs the oracle only
+(inputs from the seeded generators) and prints the table; nothing imports it."""
 
 import os
 import sys
