@@ -72,3 +72,22 @@ def check(X, Q, k, delta=0.01, seed=0, queries=None, h=None, bound="footnote", c
         summ["max_rel_S"] = max(summ["max_rel_S"], float(rel.max()))
         summ["queries"] += 1
     return summ, gpu
+
+
+def replay_row(X, q_row, g, k, qid, storage="f32", delta=0.01, seed=0, **opt):
+    """Oracle replay of one query's decision log; `g` holds that query's
+    numpy rows (code, S, evals, count, rounds) from a traced GPU call.
+    Returns the oracle's stats and the largest relative error of S."""
+    oopt = {kk: v for kk, v in opt.items() if kk in ("h", "bound", "c_alpha", "B0", "B", "grow")}
+    p = oracle.make_params(k, delta=delta, seed=seed, qid=qid, tol=TOL_DECISION, storage=storage, **oopt)
+    o = oracle.adaptive(X, q_row[None, :], p, replay=g["code"][None, :])
+    st = o["stats"][0]
+    assert st["mismatch"] == 0 and st["log_inconsistent"] == 0, (qid, st)
+    np.testing.assert_array_equal(o["code"][0], g["code"])
+    assert int(g["evals"]) == st["evals"] and int(g["count"]) == st["count"], (qid, st)
+    assert int(g["rounds"]) == st["rounds"], (qid, st)
+    So, Sg = o["S"][0], g["S"].astype(np.float64)
+    rel = np.abs(Sg - So) / np.maximum(np.abs(So), 1e-300)
+    rel[(So == 0) & (Sg == 0)] = 0
+    assert rel.max() <= TOL_ESTIMATE, (qid, rel.max())
+    return st, float(rel.max()), o

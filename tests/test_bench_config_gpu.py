@@ -1,0 +1,67 @@
+"""The benchmark's own timed configuration, replayed in the oracle.
+
+Workload: pixel mixture, n = 100,000 points in d = 784, 1,024 queries, k = 10,
+delta = 0.01 (the inputs bench.py generates). Path: a resident dataset, the
+point-major round-0 pass and the round-0 filter, rounds B0 = B = 8 doubling,
+1,024 threads per query, the Section 5 bound with C_alpha = 1e-3, rounds and
+FP64 rerank captured in one CUDA graph (runtime.GraphStep) — the step bench.py
+times. Sampled queries (first, middle, last, and two more) then run alone
+through the same dataset path with their decision log and Philox query id,
+must equal their row of the graph's batch, and are replayed round by round
+in the oracle: decisions, evaluation counts and rounds bit-exact outside the
+near-threshold band, sums within 1e-5 relative of FP64, and the reranked top
+k equal to the oracle's brute force."""
+
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from _parity import replay_row
+from paper_1902_09465_gb300 import knn, runtime
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BENCH_OPTS = dict(bound="exp", c_alpha=1e-3, B0=8, B=8, grow=1, threads=1024)
+
+
+def test_benchmark_timed_configuration_replayed():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    w = bench.WORKLOAD
+    X, Q, _ = bench.make_inputs(0)
+    k = w["k"]
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    with knn.Dataset(Xd, copies=()) as ds:
+        step = runtime.GraphStep(ds, w["nq"], k, delta=w["delta"], seed=0, storage="f32", **BENCH_OPTS)
+        res, ri, rd = step.run(Qd)
+        torch.cuda.synchronize()
+        batch = {key: v.cpu().numpy() for key, v in res.items()}
+        ri, rd = ri.cpu().numpy(), rd.cpu().numpy()
+        picks = (0, 1, w["nq"] // 2, w["nq"] - 2, w["nq"] - 1)
+        ti, td = oracle.exact_knn(X, Q[list(picks)], k)
+        near = 0
+        for j, q in enumerate(picks):
+            r = ds.adaptive(Qd[q:q + 1], k, w["delta"], 0, storage="f32", trace=True, qid_base=q, **BENCH_OPTS)
+            torch.cuda.synchronize()
+            g = {key: v[0].cpu().numpy() for key, v in r.items()}
+            for key in ("count", "evals", "rounds"):
+                assert int(g[key]) == int(batch[key][q]), (q, key)
+            c = int(g["count"])
+            assert np.array_equal(g["idx"][:c], batch["idx"][q, :c])
+            assert np.all(batch["idx"][q, c:] == -1)
+            st, _, _ = replay_row(X, Q[q], g, k, q, delta=w["delta"], **BENCH_OPTS)
+            near += st["near"]
+            # the reranked k nearest of the graph step against the oracle's brute force
+            np.testing.assert_allclose(rd[q], td[j], rtol=1e-12)
+            for a_, b_ in zip(ri[q], ti[j]):   # equal up to exact-distance ties
+                if a_ != b_:
+                    da = float(((X[a_].astype(np.float64) - Q[q]) ** 2).sum())
+                    db = float(((X[b_].astype(np.float64) - Q[q]) ** 2).sum())
+                    assert abs(da - db) <= 1e-12 * db, (q, a_, b_)
+        assert near <= 5 * len(picks)
