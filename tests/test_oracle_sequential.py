@@ -93,3 +93,45 @@ def test_vanishing_bounds_stop_before_the_first_iteration(heaps):
                     for i, j in ((i, oracle.coordinate(5, 7, i, 0, m)) for i in range(n))])
     want = np.lexsort((np.arange(n), est))[: k + h]
     np.testing.assert_array_equal(idx, want)
+
+
+def _cost_table(name, gen, k, h, delta, c_alpha, trials, schedules):
+    """Medians of evaluations / (n m) of Algorithm 1 (seven heaps) and of the
+    batched rounds at each schedule, with how often the k nearest came back."""
+    rows = {"sequential": [], **{s: [] for s in schedules}}
+    hits = {key: 0 for key in rows}
+    for t in range(trials):
+        X, Q = gen(t)
+        n, m = X.shape
+        true = set(oracle.exact_knn(X, Q[:1], k)[0][0].tolist())
+        p = oracle.make_params(k, h=h, delta=delta, bound="exp", c_alpha=c_alpha, seed=t)
+        idx, ev, _ = oracle.sequential(X, Q[0], p, heaps=True)
+        rows["sequential"].append(ev / (n * m))
+        hits["sequential"] += true <= set(idx.tolist())
+        for b0, b, g in schedules:
+            pb = oracle.make_params(k, h=h, delta=delta, bound="exp", c_alpha=c_alpha, seed=t, B0=b0, B=b, grow=g)
+            st = oracle.adaptive(X, Q[:1], pb, want_state=False)
+            s0 = st["stats"][0]
+            rows[(b0, b, g)].append(s0["evals"] / (n * m))
+            hits[(b0, b, g)] += true <= set(st["idx"][0][: s0["count"]].tolist())
+    med = {key: float(np.median(v)) for key, v in rows.items()}
+    print(f"\n{name}: " + ", ".join(f"{key}: {med[key]:.4f} ({hits[key]}/{trials})" for key in rows))
+    return med, hits
+
+
+def test_two_arms_per_iteration_spend_fewer_evaluations_than_batched_rounds():
+    """The cost of batching (Section 4's Algorithm 1 samples only q1 and b2 per
+    iteration): on the same inputs and bound, Algorithm 1 spends fewer
+    coordinate evaluations than rounds that sample every undecided point,
+    and both return the k nearest. (python -m pytest -s prints the medians.)"""
+    sched = ((1, 1, 0), (8, 8, 1), (16, 16, 1))
+    med, hits = _cost_table("gaussian planted n = 2,000, m = 256, k = h = 5, C_alpha = 1e-3",
+                            lambda t: synth.gaussian_planted(2000, 256, 5, seed=t)[:2], 5, 5, 0.01, 1e-3, 6, sched)
+    for s in sched:
+        assert med["sequential"] < med[s]
+    assert all(v == 6 for v in hits.values())
+    med, hits = _cost_table("subspace p = 10, n = 1,000, m = 12,288, k = h = 10, C_alpha = 1e-3",
+                            lambda t: synth.subspace(1000, 12288, 10, nq=1, seed=t), 10, 10, 0.001, 1e-3, 3, sched)
+    for s in sched:
+        assert med["sequential"] < med[s]
+    assert all(v == 3 for v in hits.values())
