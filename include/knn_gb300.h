@@ -205,7 +205,10 @@ knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m, const floa
  *   copy (same outputs, same workspace size as knn_adaptive).
  */
 typedef struct knn_dataset knn_dataset;
-enum { KNN_COPY_SCREEN = 1 << 3 };
+/* Operands of knn_exact_ds's tensor-core screens (see there): BF16 hi/lo
+ * split (KNN_SCREEN_BF16X3), FP16 scaled by a power of two (KNN_SCREEN_F16),
+ * single BF16 (KNN_SCREEN_BF16). */
+enum { KNN_COPY_SCREEN = 1 << 3, KNN_COPY_SCREEN_F16 = 1 << 4, KNN_COPY_SCREEN_BF16 = 1 << 5 };
 knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, int32_t copies, void* stream,
                               knn_dataset** out);
 knn_status knn_dataset_destroy(knn_dataset* ds);
@@ -253,11 +256,16 @@ knn_status knn_adaptive_ds_multi(const knn_dataset* ds, int32_t storage, const f
 /*
  * knn_rerank -- exact distances of candidate points, then top-k.
  *
- * For each query q, computes d = sum_j (X[c,j] - Q[q,j])^2 in FP64 for each
- * candidate c = cand[q, t] (t < ncand; entries < 0 are skipped; the valid
- * entries of a row must be distinct: a repeated index is ranked twice) and returns
- * the k smallest by (d, index) (Section 3's brute force restricted to the
+ * For each query q, returns the k candidates c = cand[q, t] (t < ncand;
+ * entries < 0 are skipped; the valid entries of a row must be distinct: a
+ * repeated index is ranked twice) with the smallest d = sum_j (X[c,j] -
+ * Q[q,j])^2 by (d, index) (Section 3's brute force restricted to the
  * candidates; the last step of returning the k nearest from the set S-hat).
+ * Every candidate's distance is taken in FP32 (relative error at most
+ * gamma_(m+2)); only the candidates whose FP32 distance lies within that
+ * error of the k-th one are recomputed in FP64 and ranked, which gives the
+ * same result as ranking every candidate in FP64. A row whose first entry is
+ * -2 ranks every point instead.
  * out_idx: nq x k int64 (-1 padded when fewer valid candidates);
  * out_dist: nq x k float64 squared distances (+inf padded).
  * ncand <= 4096. No workspace.
@@ -299,18 +307,36 @@ knn_status knn_exact_l1(const float* X, int64_t n, int32_t m, const float* Q, in
  * knn_exact_ds -- the naive exact method over a resident dataset, with a
  * choice of screen:
  *   KNN_SCREEN_F32     the FP32 SIMT screen of knn_exact;
- *   KNN_SCREEN_BF16X3  a tcgen05 tensor-core GEMM on the centred data split
- *                      into BF16 hi + lo parts (three products per pair,
- *                      FP32 accumulation in tensor memory); needs a dataset
- *                      created with KNN_COPY_SCREEN and an sm_10x device.
- * Both keep every point within twice the screen's proven error bound of the
- * k-th screened value and rerank those in FP64 (knn_rerank), so the result
- * is exact: the k nearest by (distance, index).
+ *   KNN_SCREEN_F16     a tcgen05 tensor-core GEMM of the centred data and
+ *                      queries, each scaled by a power of two and rounded to
+ *                      FP16 (FP32 accumulation in tensor memory); needs
+ *                      KNN_COPY_SCREEN_F16;
+ *   KNN_SCREEN_BF16    the same GEMM on values rounded to BF16; needs
+ *                      KNN_COPY_SCREEN_BF16;
+ *   KNN_SCREEN_BF16X3  the same GEMM on the centred data split into BF16
+ *                      hi + lo parts (three products per pair); needs
+ *                      KNN_COPY_SCREEN.
+ * The tensor-core screens (sm_10x devices) select inside the GEMM: a first
+ * pass over a subset of the points bounds each query's k-th screened value
+ * from above, a second pass appends every pair within twice the screen's
+ * proven error bound of that bound to the query's candidate list (no n x nq
+ * matrix is written); the FP32 screen writes the matrix and selects. All
+ * keep every true k-nearest point and rank the candidates as knn_rerank does,
+ * so the result is exact: the k nearest by (distance, index). A query whose
+ * candidates overflow the list is ranked over every point.
  */
-enum { KNN_SCREEN_F32 = 0, KNN_SCREEN_BF16X3 = 1 };
+enum { KNN_SCREEN_F32 = 0, KNN_SCREEN_BF16X3 = 1, KNN_SCREEN_F16 = 2, KNN_SCREEN_BF16 = 3 };
 size_t knn_exact_ds_workspace_size(const knn_dataset* ds, int32_t screen, int32_t nq);
 knn_status knn_exact_ds(const knn_dataset* ds, int32_t screen, const float* Q, int32_t nq, int32_t k,
                         int64_t* out_idx, double* out_dist, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Failure detection, a test hook (no counterpart in the paper): the
+ * tensor-core kernels' pipeline waits give up after `tries` polls of their
+ * barrier (tries < 0 restores the default, about a second). A wait that gives
+ * up records a code read by knn_device_status; its call's outputs are then
+ * invalid. With 0 every such wait gives up at once, before any copy or
+ * matrix multiply is issued. Applies to calls made after it. */
+knn_status knn_debug_wait_limit(int64_t tries);
 
 /* Library status of the current device: 0, or a nonzero code recorded by a
  * kernel that gave up a bounded wait (the call's outputs are then invalid).

@@ -23,7 +23,7 @@ extern template KNN_DS_LAUNCH_DECL(Blk<ElemFP8>);
 
 namespace knn {
 
-knn_status build_screen_operand(knn_dataset* ds, cudaStream_t stream);
+knn_status build_screen_operand(knn_dataset* ds, int32_t copies, cudaStream_t stream);
 
 // BF16 copy (round to nearest even) and its largest element error.
 static __global__ void quantize_bf16_kernel(const float* __restrict__ X, size_t count, uint16_t* __restrict__ out,
@@ -107,8 +107,9 @@ extern "C" knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, i
   *out = nullptr;
   if (n < 1 || n >= (int64_t)1 << 31 || m < 1 || m > kMaxM)
     return set_error("knn_dataset_create: need 1 <= n < 2^31 and 1 <= m <= 16384"), KNN_EINVAL;
-  if (copies & ~((1 << KNN_STORE_BF16) | (1 << KNN_STORE_FP8) | KNN_COPY_SCREEN))
-    return set_error("knn_dataset_create: copies must be a mask of BF16, FP8 and the screen operand"), KNN_EINVAL;
+  const int32_t screens = KNN_COPY_SCREEN | KNN_COPY_SCREEN_F16 | KNN_COPY_SCREEN_BF16;
+  if (copies & ~((1 << KNN_STORE_BF16) | (1 << KNN_STORE_FP8) | screens))
+    return set_error("knn_dataset_create: copies must be a mask of BF16, FP8 and the screen operands"), KNN_EINVAL;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   knn_dataset* ds = new knn_dataset();
   ds->X = X;
@@ -138,7 +139,7 @@ extern "C" knn_status knn_dataset_create(const float* X, int64_t n, int32_t m, i
       quantize_fp8_kernel<<<di.sms * 8, 256, 0, stream>>>(X, n, m, ds->x8, ds->scale8, ds->emax + KNN_STORE_FP8);
     s = cuda_check(cudaGetLastError(), "dataset kernels launch");
   }
-  if (s == KNN_OK && (copies & KNN_COPY_SCREEN)) s = build_screen_operand(ds, stream);
+  if (s == KNN_OK && (copies & screens)) s = build_screen_operand(ds, copies, stream);
   if (s == KNN_OK) s = cuda_check(cudaStreamSynchronize(stream), "dataset build");
   if (s == KNN_OK) {
     unsigned bits[3];
@@ -165,6 +166,8 @@ extern "C" knn_status knn_dataset_destroy(knn_dataset* ds) {
   cudaFree(ds->x8);
   cudaFree(ds->scale8);
   cudaFree(ds->screenA);
+  cudaFree(ds->screen16);
+  cudaFree(ds->screenb);
   cudaFree(ds->mu);
   cudaFree(ds->xcn);
   cudaFree(ds->xcn_max);

@@ -19,8 +19,8 @@ namespace knn {
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
                          int32_t metric = KNN_METRIC_L2SQ);
-size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq);
-knn_status exact_tc(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k, int64_t* out_idx,
+size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq, int32_t screen);
+knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32_t nq, int32_t k, int64_t* out_idx,
                     double* out_dist, void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 constexpr int kExactCand = 2048;  // candidate slots per query before falling back to a full scan
@@ -346,7 +346,8 @@ extern "C" knn_status knn_exact(const float* X, int64_t n, int32_t m, const floa
 
 extern "C" size_t knn_exact_ds_workspace_size(const knn_dataset* ds, int32_t screen, int32_t nq) {
   if (!ds) return 0;
-  if (screen == KNN_SCREEN_BF16X3) return exact_tc_workspace(ds->n, ds->m, nq);
+  if (screen == KNN_SCREEN_BF16X3 || screen == KNN_SCREEN_F16 || screen == KNN_SCREEN_BF16)
+    return exact_tc_workspace(ds->n, ds->m, nq, screen);
   return knn_exact_workspace_size(ds->n, ds->m, nq, 1);
 }
 
@@ -357,13 +358,13 @@ extern "C" knn_status knn_exact_ds(const knn_dataset* ds, int32_t screen, const 
   if (!ds) return set_error("knn_exact_ds: null dataset"), KNN_EINVAL;
   if (k < 1 || k > ds->n || k > kMaxKH || nq < 0)
     return set_error("knn_exact_ds: need 1 <= k <= min(n, 1024), nq >= 0"), KNN_EINVAL;
-  if (screen != KNN_SCREEN_F32 && screen != KNN_SCREEN_BF16X3)
+  if (screen != KNN_SCREEN_F32 && screen != KNN_SCREEN_BF16X3 && screen != KNN_SCREEN_F16 && screen != KNN_SCREEN_BF16)
     return set_error("knn_exact_ds: unknown screen"), KNN_EINVAL;
   if (nq == 0) return KNN_OK;
   if (!Q || !out_idx || !out_dist) return set_error("knn_exact_ds: null pointer"), KNN_EINVAL;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-  if (screen == KNN_SCREEN_BF16X3)
-    return exact_tc(ds, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream);
+  if (screen != KNN_SCREEN_F32)
+    return exact_tc(ds, screen, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream);
   return knn_exact(ds->X, ds->n, ds->m, Q, nq, k, out_idx, out_dist, workspace, workspace_bytes, stream_);
 }
 

@@ -86,12 +86,15 @@ struct knn_dataset {
   float* scale8 = nullptr;    // FP8 per-row scale
   unsigned* emax = nullptr;   // [3]: largest |copy - X| per storage, as float bits
   float emax_host[3] = {0.0f, 0.0f, 0.0f};
-  // tensor-core screen operand: rows [hi | hi | lo] of (x - mu), each part Kp wide
+  // tensor-core screen operands of x - mu, each part Kp wide: BF16x3 rows
+  // [hi | hi | lo], single FP16 rows (scaled by a power of two), single BF16 rows
   int32_t Kp = 0;
   uint16_t* screenA = nullptr;
+  uint16_t* screen16 = nullptr;
+  uint16_t* screenb = nullptr;
   float* mu = nullptr;        // column means
   float* xcn = nullptr;       // ||x_i - mu||^2
-  unsigned* xcn_max = nullptr;  // largest of them, float bits
+  unsigned* xcn_max = nullptr;  // [2]: largest ||x_i - mu||^2, largest |x_ij - mu_j| (float bits)
   // shared-coordinate copies for one seed: column t holds column jperm[t]
   uint64_t share_seed = 0;
   int32_t share_ready = 0;    // bit s set: the copy of storage s is built

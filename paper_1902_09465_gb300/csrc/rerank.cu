@@ -1,7 +1,9 @@
-// rerank.cu -- exact FP64 distances of candidate points and top-k selection
-// (the brute force of Section 3 restricted to a candidate set, e.g. the set
-// S-hat returned by the adaptive rounds). The only double-precision
-// arithmetic of the library.
+// rerank.cu -- exact k nearest of candidate points (the brute force of
+// Section 3 restricted to a candidate set, e.g. the set S-hat returned by the
+// adaptive rounds, or the candidates of the exact method's screen): FP32
+// distances of every candidate, FP64 only for those the FP32 error bound
+// cannot separate from the k-th. The only double-precision arithmetic of the
+// library.
 #include <cfloat>
 #include <cmath>
 
@@ -52,69 +54,175 @@ __device__ __forceinline__ double row_dist64(const float* xr, const float* qs, i
   return s;
 }
 
-// One CTA per query. cand[q*ncand + t]: candidate indices (< 0 skipped). A
-// row whose first entry is -2 asks for every point (used when a screen
-// could not bound its candidate set); the points are then taken in chunks
-// and merged with the running top-k.
+// FP32 distance of one row, one warp: squared l2 or l1, each term and the
+// sum in FP32 (within a relative error gamma_(m+2) of the exact distance:
+// one rounding for the difference, one for the square, m - 1 additions).
+__device__ __forceinline__ float row_dist32(const float* xr, const float* qs, int m, int lane, bool l1, bool vec) {
+  float s = 0.0f;
+  if (vec) {
+    for (int j = lane * 4; j < m; j += 128) {
+      const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr + j));
+      const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+      const float d0 = x4.x - q4.x, d1 = x4.y - q4.y, d2 = x4.z - q4.z, d3 = x4.w - q4.w;
+      if (l1) {
+        s += fabsf(d0);
+        s += fabsf(d1);
+        s += fabsf(d2);
+        s += fabsf(d3);
+      } else {
+        s = fmaf(d0, d0, s);
+        s = fmaf(d1, d1, s);
+        s = fmaf(d2, d2, s);
+        s = fmaf(d3, d3, s);
+      }
+    }
+  } else {
+    for (int j = lane; j < m; j += 32) {
+      const float d = __ldg(xr + j) - qs[j];
+      s = l1 ? s + fabsf(d) : fmaf(d, d, s);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 template <int NT>
-__global__ void __launch_bounds__(NT) rerank_kernel(const float* __restrict__ X, int64_t n, int m,
+__device__ void bitonic_sort_u64(uint64_t* key, int P) {
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (P >> 1); i += NT) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t a = key[lo], b = key[hi];
+        if ((b < a) == up) {
+          key[lo] = b;
+          key[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// One CTA per query: the exact k nearest of a candidate list by (distance,
+// index). Candidates: cand[q*ncand + t] for t < ncand (entries < 0 skipped),
+// or t < cnt[q] when counts are given.
+//   1. FP32 distance d32 of every candidate (relative error <= rel);
+//   2. tau32 = the k-th smallest d32; every candidate whose distance is at
+//      most the k-th true one has d32 <= tau32 (1 + rel) / (1 - rel) (k
+//      candidates have d <= tau32 / (1 - rel));
+//   3. FP64 distances of that window only, top-k by (d64, index).
+// A list that overflowed (cnt[q] > ncand, or a first entry of -2) asks for
+// every point instead: points stream in index order, FP64 only for those
+// whose d32 can still reach the running k-th distance, merged with the
+// running top-k chunk by chunk.
+template <int NT>
+__global__ void __launch_bounds__(NT) refine_kernel(const float* __restrict__ X, int64_t n, int m,
                                                     const float* __restrict__ Q, const int64_t* __restrict__ cand,
-                                                    int ncand, int k, int64_t* out_idx, double* out_dist,
-                                                    int l1) {
+                                                    int ncand, const int32_t* __restrict__ cnt, int k,
+                                                    int64_t* out_idx, double* out_dist, int l1, int vec, int cap) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
-  int64_t* idx = reinterpret_cast<int64_t*>(key + kRerankCap);
-  float* qs = reinterpret_cast<float*>(idx + kRerankCap);
+  int64_t* idx = reinterpret_cast<int64_t*>(key + cap);
+  uint64_t* k32 = reinterpret_cast<uint64_t*>(idx + cap);
+  float* qs = reinterpret_cast<float*>(k32 + cap);
+  __shared__ int s_cnt;
   const int q = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t kInf = 0x7FF0000000000000ULL;
+  const float u = 1.0f / 16777216.0f;
+  const float rel = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);
   for (int j = threadIdx.x; j < m; j += NT) qs[j] = Q[(size_t)q * m + j];
   const int64_t* cr = cand + (size_t)q * ncand;
-  const bool full = ncand > 0 && cr[0] == -2;
+  const int c = cnt ? min(cnt[q], ncand + 1) : ncand;
+  const bool full = c > ncand || (ncand > 0 && c > 0 && cr[0] == -2);
   __syncthreads();
   if (!full) {
-    const int P = next_pow2(ncand < 2 ? 2 : ncand);
-    for (int t = threadIdx.x; t < P; t += NT) {
+    // 1. FP32 distances, keyed (d32 bits, slot)
+    const int P = next_pow2(c < 2 ? 2 : c);
+    for (int t = threadIdx.x; t < P; t += NT) k32[t] = ~0ull;
+    __syncthreads();
+    for (int t = warp; t < c; t += NT / 32) {
+      const int64_t id = cr[t];
+      if (id < 0 || id >= n) continue;
+      const float d = row_dist32(X + (size_t)id * m, qs, m, lane, l1 != 0, vec != 0);
+      if (lane == 0 && !isnan(d)) k32[t] = ((uint64_t)f2key(d) << 32) | (uint32_t)t;
+    }
+    __syncthreads();
+    bitonic_sort_u64<NT>(k32, P);
+    // 2. the window: a prefix of the sorted keys
+    int v = 0;
+    for (int b = 0; b < P; b += NT) v += __syncthreads_count(b + threadIdx.x < P && k32[b + threadIdx.x] != ~0ull);
+    const int kk = min(k, v);
+    int w = 0;
+    if (kk > 0) {
+      const float tau = key2f((uint32_t)(k32[kk - 1] >> 32));
+      const float thr = tau * ((1.0f + rel) / (1.0f - rel)) * (1.0f + 4.0f * u);
+      for (int b = 0; b < v; b += NT)
+        w += __syncthreads_count(b + threadIdx.x < v && key2f((uint32_t)(k32[b + threadIdx.x] >> 32)) <= thr);
+    }
+    // 3. FP64 distances of the window
+    const int P2 = next_pow2(w < 2 ? 2 : w);
+    for (int t = threadIdx.x; t < P2; t += NT) {
       key[t] = kInf;
       idx[t] = INT64_MAX;
     }
     __syncthreads();
-    for (int t = warp; t < ncand; t += NT / 32) {
-      const int64_t c = cr[t];
-      if (c < 0 || c >= n) continue;
-      const double d = row_dist64(X + (size_t)c * m, qs, m, lane, l1 != 0);
+    for (int t = warp; t < w; t += NT / 32) {
+      const int64_t id = cr[(uint32_t)k32[t]];
+      const double d = row_dist64(X + (size_t)id * m, qs, m, lane, l1 != 0);
       if (lane == 0) {
         key[t] = (uint64_t)__double_as_longlong(d);
-        idx[t] = c;
+        idx[t] = id;
       }
     }
     __syncthreads();
-    bitonic_sort_pairs<NT>(key, idx, P);
+    bitonic_sort_pairs<NT>(key, idx, P2);
   } else {
-    // running top-k in [0, k), next chunk of points in [k, kRerankCap)
-    for (int t = threadIdx.x; t < kRerankCap; t += NT) {
+    // running top-k in [0, k), the chunk's admitted points after it
+    for (int t = threadIdx.x; t < cap; t += NT) {
       key[t] = kInf;
       idx[t] = INT64_MAX;
     }
     __syncthreads();
-    const int chunk = kRerankCap - k;
+    const int chunk = cap - k;
+    float thr32 = INFINITY;
     for (int64_t base = 0; base < n; base += chunk) {
-      for (int t = k + threadIdx.x; t < kRerankCap; t += NT) {
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
+      for (int t = warp; t < chunk; t += NT / 32) {
+        const int64_t id = base + t;
+        if (id >= n) break;
+        const float d32 = row_dist32(X + (size_t)id * m, qs, m, lane, l1 != 0, vec != 0);
+        if (d32 <= thr32) {  // warp-uniform
+          const double d = row_dist64(X + (size_t)id * m, qs, m, lane, l1 != 0);
+          if (lane == 0) {
+            const int p = atomicAdd(&s_cnt, 1);
+            key[k + p] = (uint64_t)__double_as_longlong(d);
+            idx[k + p] = id;
+          }
+        }
+      }
+      __syncthreads();
+      const int used = k + s_cnt;
+      const int P = next_pow2(used < 2 ? 2 : used);
+      for (int t = used + threadIdx.x; t < P; t += NT) {
         key[t] = kInf;
         idx[t] = INT64_MAX;
       }
       __syncthreads();
-      for (int t = warp; t < chunk; t += NT / 32) {
-        const int64_t c = base + t;
-        if (c >= n) break;
-        const double d = row_dist64(X + (size_t)c * m, qs, m, lane, l1 != 0);
-        if (lane == 0) {
-          key[k + t] = (uint64_t)__double_as_longlong(d);
-          idx[k + t] = c;
-        }
+      bitonic_sort_pairs<NT>(key, idx, P);
+      // a later point (larger index) enters only with a smaller distance:
+      // d32 <= d (1 + rel) <= d64_k (1 + rel)
+      if (key[k - 1] != kInf)
+        thr32 = __double2float_ru(__longlong_as_double((long long)key[k - 1]) * (1.0 + (double)rel) * (1.0 + 1e-9));
+      for (int t = k + threadIdx.x; t < P; t += NT) {
+        key[t] = kInf;
+        idx[t] = INT64_MAX;
       }
       __syncthreads();
-      bitonic_sort_pairs<NT>(key, idx, kRerankCap);
     }
   }
   for (int t = threadIdx.x; t < k; t += NT) {
@@ -124,17 +232,28 @@ __global__ void __launch_bounds__(NT) rerank_kernel(const float* __restrict__ X,
   }
 }
 
+knn_status launch_refine(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
+                         int32_t ncand, const int32_t* cnt, int32_t k, int64_t* out_idx, double* out_dist,
+                         cudaStream_t stream, int32_t metric) {
+  // sort capacity: every candidate, and room for a chunk of points beside the
+  // running top-k when a list asks for every point
+  int cap = 2;
+  while (cap < ncand || cap < 2 * k + 256) cap <<= 1;
+  const size_t smem = (size_t)cap * 24 + (size_t)m * 4;
+  knn_status s = cuda_check(
+      cudaFuncSetAttribute(refine_kernel<kRerankNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+      "cudaFuncSetAttribute(refine)");
+  if (s != KNN_OK) return s;
+  const int vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
+  refine_kernel<kRerankNT><<<nq, kRerankNT, smem, stream>>>(X, n, m, Q, cand, ncand, cnt, k, out_idx, out_dist,
+                                                            metric == KNN_METRIC_L1 ? 1 : 0, vec, cap);
+  return cuda_check(cudaGetLastError(), "refine_kernel launch");
+}
+
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
                          int32_t metric) {
-  const size_t smem = (size_t)kRerankCap * 16 + (size_t)m * 4;
-  knn_status s = cuda_check(
-      cudaFuncSetAttribute(rerank_kernel<kRerankNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-      "cudaFuncSetAttribute(rerank)");
-  if (s != KNN_OK) return s;
-  rerank_kernel<kRerankNT><<<nq, kRerankNT, smem, stream>>>(X, n, m, Q, cand, ncand, k, out_idx, out_dist,
-                                                            metric == KNN_METRIC_L1 ? 1 : 0);
-  return cuda_check(cudaGetLastError(), "rerank_kernel launch");
+  return launch_refine(X, n, m, Q, nq, cand, ncand, nullptr, k, out_idx, out_dist, stream, metric);
 }
 
 }  // namespace knn

@@ -1,29 +1,48 @@
-// screen_tc.cu -- the naive exact method's screen as a tcgen05 tensor-core
-// GEMM (Section 3: all distances, then select; the select and the FP64 rerank
-// are in exact.cu and rerank.cu).
+// screen_tc.cu -- the naive exact method (Section 3: every distance, then
+// select) as a tcgen05 tensor-core GEMM with the selection fused into its
+// epilogue, followed by an FP32 refine and an FP64 rerank of near ties
+// (rerank.cu).
 //
 // Distances are translation invariant, so the data is centred on its column
-// mean mu once (xc = x - mu) and each centred value is split into two BF16
-// parts, xc = hi + lo + r with |r| <= 2^-18 |xc|. One BF16 GEMM over the
-// concatenated rows [hi | hi | lo] . [qhi | qlo | qhi] then gives
-// hi.qhi + hi.qlo + lo.qhi, the product of the centred vectors up to
-// 3.1 * 2^-18 sum|xc||qc| plus the accumulation error; the screened distance
-// is ||xc||^2 + ||qc||^2 - 2 xc.qc and its error bound is applied by the
-// select kernel.
+// mean mu once (xc = x - mu) and the screened distance of a pair is
+//   D~ = fl(||xc||^2 + ||qc||^2 + c2 * acc),   acc ~ sum_j xc^_j qc^_j,
+// acc accumulated in FP32 in tensor memory over 16-bit operands xc^, qc^ of
+// one of three kinds:
+//   F16     xc and qc scaled by powers of two (max |.| in [2^14, 2^15)) and
+//           rounded to FP16 (u = 2^-11): K = m, c2 = -2 / (scales);
+//   BF16    rounded to BF16 (u = 2^-8): K = m, c2 = -2;
+//   BF16X3  split xc = hi + lo + r (|r| <= 2^-18 |xc|), the concatenated rows
+//           [hi | hi | lo] . [qhi | qlo | qhi]: K = 3m, c2 = -2.
+// |D~ - d| <= E_q, a bound from the operand rounding, the FP32 accumulation
+// and the norms' FP32 sums (exact_tc below).
 //
-// GEMM: one CTA per 128-point x 256-query tile, 128 threads, two CTAs per
-// SM (about 97 KB of shared memory and 256 TMEM columns each, so one CTA's
-// epilogue overlaps the other's main loop). Warp 0 lane 0 issues TMA loads
-// (128-byte swizzle, 64 K-elements per stage, 2 stages),
-// warp 1 lane 0 issues tcgen05.mma (M=128, N=256, K=16, BF16 x BF16 -> FP32
-// in TMEM) and commits each stage back to the producer; all four warps then
-// read their 32 TMEM lanes (tcgen05.ld 32x32b) and write the screened values.
-// Every mbarrier wait is bounded; a wait that gives up records an error in
-// the library status word and the CTA still frees its TMEM before it exits.
+// Two passes of one persistent kernel avoid writing the nq x n matrix:
+//   pass 1  every s-th tile of 128 points: the smallest D~ of each group of 32
+//           points, per query (group minima come from distinct points, so the
+//           k-th smallest of them bounds the k-th smallest D~ from above);
+//   cut     tau_q = that k-th smallest, cut_q = tau_q + 2 E_q (screen_cut_kernel);
+//   pass 2  every tile: each pair with D~ <= cut_q joins the query's candidate
+//           list (atomic append; a full list marks the query for a full scan).
+// Every true k-nearest point j is kept: k points have D~ <= tau_q, so the
+// k-th true distance is at most tau_q + E_q, and d_j <= that gives
+// D~_j <= d_j + E_q <= cut_q.
+//
+// Kernel layout: one CTA per SM, persistent over tiles of 128 points x 256
+// queries, 6 warps. Warp 0 lane 0 issues TMA loads (128-byte swizzle, 64
+// K-elements per stage, 4 stages); warp 1 lane 0 issues tcgen05.mma (M = 128,
+// N = 256, K = 16, FP32 accumulator in TMEM) into one of two accumulators of
+// 256 columns, so the epilogue of one tile overlaps the MMAs of the next;
+// warps 2-5 read the accumulator (tcgen05.ld 32x32b, one TMEM lane quarter
+// each) and run the pass's epilogue. Every mbarrier wait is bounded: a wait
+// that gives up records a code in the library status word, the CTA waits for
+// its TMA copies and MMAs in flight and frees its tensor memory before it exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -33,20 +52,23 @@
 
 namespace knn {
 
-knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
-                         int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
-                         int32_t metric = KNN_METRIC_L2SQ);
-knn_status launch_screen_select(float* D, int64_t n, int32_t nq, int32_t m, int32_t k, const float* qn,
-                                const unsigned* xn_max_bits, double c_cross, double c_square, const float* X,
-                                const float* Q, int64_t* cand,
-                                cudaStream_t stream);
-constexpr int kExactCandTc = 2048;
+knn_status launch_refine(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
+                         int32_t ncand, const int32_t* cnt, int32_t k, int64_t* out_idx, double* out_dist,
+                         cudaStream_t stream, int32_t metric);
 
-constexpr int kTcM = 128, kTcN = 256, kTcK = 64, kTcStages = 2, kTcThreads = 128;
+constexpr int kTcM = 128, kTcN = 256, kTcK = 64, kTcStages = 4, kTcThreads = 192;
 constexpr int kTcABytes = kTcM * kTcK * 2;  // 16 KB
 constexpr int kTcBBytes = kTcN * kTcK * 2;  // 32 KB
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr int kTcCols = 2 * kTcN;           // two accumulators of 256 FP32 columns
+constexpr int kScreenCap = 2048;            // candidate slots per query
+constexpr int kStage = 8;                   // pairs of a query column staged per tile in shared memory
+constexpr uint32_t kSpinDefault = 1u << 26;
 constexpr int kStatusTimeout = 0x5C7C;      // recorded when a bounded wait gives up
+
+// Tries of the pipeline waits (a test hook; see knn_debug_wait_limit).
+static std::atomic<uint32_t> g_wait_limit{kSpinDefault};
+
+enum ScreenKind { kKindF16 = 0, kKindBF16 = 1, kKindBF16x3 = 2 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -55,6 +77,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
@@ -67,9 +92,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Waits for the phase of `parity` to complete; false after kSpinLimit tries.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i)
+// Waits for the phase of `parity` to complete; false after `limit` tries.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -95,17 +120,21 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, N = 256, M = 128.
-constexpr uint32_t kIdescBf16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                                ((uint32_t)(kTcM >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B types at bits 7-9 and 10-12 (0 = F16, 1 = BF16), both K-major, N >> 3 at
+// bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16kind(bool bf16) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+         ((uint32_t)(kTcM >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void umma_f16kind(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(kIdescBf16), "r"(accum)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
       : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -124,35 +153,107 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2)
-    screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int64_t n,
-                     int nq, int Kt, const float* __restrict__ xn, const float* __restrict__ qn, float* __restrict__ D,
-                     int* status) {
+// OR of a predicate over the 128 epilogue threads (named barrier 1).
+__device__ __forceinline__ bool epi_any(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)p)
+      : "memory");
+  return r != 0;
+}
+
+// Minimum over the 32 lanes of each of 16 values: halve the set per step
+// (lanes of the upper half keep the upper values), 16 shuffles in all. On
+// return the lane pair (2c, 2c + 1) holds the minimum of value c.
+__device__ __forceinline__ float warp_min16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const bool up = lane & 16;
+    const float keep = up ? v[j + 8] : v[j], send = up ? v[j] : v[j + 8];
+    v[j] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 16));
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool up = lane & 8;
+    const float keep = up ? v[j + 4] : v[j], send = up ? v[j] : v[j + 4];
+    v[j] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 8));
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const bool up = lane & 4;
+    const float keep = up ? v[j + 2] : v[j], send = up ? v[j] : v[j + 2];
+    v[j] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 4));
+  }
+  {
+    const bool up = lane & 2;
+    const float keep = up ? v[1] : v[0], send = up ? v[0] : v[1];
+    v[0] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, 2));
+  }
+  return fminf(v[0], __shfl_xor_sync(0xffffffffu, v[0], 1));
+}
+
+struct ScreenArgs {
+  int64_t n;          // points
+  int nq;             // queries
+  int nk;             // K blocks of 64 elements per row
+  int nqt;            // query tiles (256 queries each)
+  int stride;         // point tiles visited: every stride-th (pass 1), every one (pass 2)
+  int ntiles;         // tiles of this pass: ceil(point tiles / stride) x nqt
+  int pass;           // 1: group minima, 2: candidate lists
+  uint32_t idesc;     // MMA instruction descriptor (operand type)
+  uint32_t limit;     // tries of a pipeline wait before it gives up
+  const float* xn;    // [n] ||xc||^2 (FP32)
+  const float* qn;    // [nq] ||qc||^2 (FP32)
+  const float* c2;    // device scalar: -2 / (product of the operand scales)
+  float* gmin;        // pass 1: [nq][nunits] smallest D~ of each group of 32 points
+  int nunits;         // groups per query in pass 1: 4 per visited point tile
+  const float* cut;   // pass 2: [nq] cut_q
+  int* cnt;           // pass 2: [nq] candidates appended (may exceed cap)
+  int64_t* cand;      // pass 2: [nq][cap] candidate points
+  int cap;
+  int* status;        // library status word
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    screen_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                     const ScreenArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + kTcStages * kTcABytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * kTcBBytes);  // full[S], empty[S], done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
-  int* cta_err = reinterpret_cast<int*>(tmem_slot + 1);
+  // barriers: full[S], empty[S], acc_full[2], acc_empty[2], drain
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * kTcBBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 5);
+  volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* scnt = reinterpret_cast<int*>(tmem_slot + 4);                 // [256] staged pairs per column (pass 2)
+  uint8_t* srow = reinterpret_cast<uint8_t*>(scnt + kTcN);           // [256][kStage] their rows in the tile
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int q0 = blockIdx.x * kTcN;
-  const int64_t p0 = (int64_t)blockIdx.y * kTcM;
-  const int nk = Kt / kTcK;
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages), done = smem_u32(bars + 2 * kTcStages);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages);
+  const uint32_t accf0 = smem_u32(bars + 2 * kTcStages), acce0 = smem_u32(bars + 2 * kTcStages + 2);
+  const uint32_t drain = smem_u32(bars + 2 * kTcStages + 4);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(done, 1);
-    *cta_err = 0;
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 128);  // every epilogue thread arrives once per tile
+    }
+    mbar_init(drain, 1);
+    *err = 0;
+    for (int c = 0; c < kTcN; ++c) scnt[c] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(kTcN));
+                 "r"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -160,75 +261,198 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  int issued = 0;
-  if (warp == 0 && lane == 0) {  // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kTcStages;
-      const uint32_t ph = (uint32_t)(kb / kTcStages) & 1u;
-      if (!mbar_wait(empty0 + 8 * s, ph ^ 1u)) {
-        *cta_err = 1;
-        break;
+  uint32_t issued = 0;  // k-block loads the producer issued (for the clean-up)
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < a.ntiles && !*err; t += gridDim.x) {
+        const int p0 = (t / a.nqt) * a.stride * kTcM, q0 = (t % a.nqt) * kTcN;
+        for (int kb = 0; kb < a.nk; ++kb, ++it) {
+          const int s = it % kTcStages;
+          const uint32_t ph = (it / kTcStages) & 1u;
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, a.limit)) {
+            *err = 1;
+            break;
+          }
+          mbar_expect_tx(full0 + 8 * s, kTcABytes + kTcBBytes);
+          tma_load_2d(smem_u32(sA + s * kTcABytes), &mapA, full0 + 8 * s, kb * kTcK, p0);
+          tma_load_2d(smem_u32(sB + s * kTcBBytes), &mapB, full0 + 8 * s, kb * kTcK, q0);
+          issued = it + 1;
+        }
       }
-      mbar_expect_tx(full0 + 8 * s, kTcABytes + kTcBBytes);
-      tma_load_2d(smem_u32(sA + s * kTcABytes), &mapA, full0 + 8 * s, kb * kTcK, (int)p0);
-      tma_load_2d(smem_u32(sB + s * kTcBBytes), &mapB, full0 + 8 * s, kb * kTcK, q0);
-      issued = kb + 1;
     }
-  } else if (warp == 1 && lane == 0) {  // MMA issuer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kTcStages;
-      const uint32_t ph = (uint32_t)(kb / kTcStages) & 1u;
-      if (!mbar_wait(full0 + 8 * s, ph)) {
-        *cta_err = 1;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      uint32_t it = 0, tc = 0;
+      for (int t = blockIdx.x; t < a.ntiles && !*err; t += gridDim.x, ++tc) {
+        const int buf = tc & 1;
+        if (!mbar_wait(acce0 + 8 * buf, ((tc >> 1) & 1u) ^ 1u, a.limit)) {
+          *err = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * kTcN);
+        bool ok = true;
+        for (int kb = 0; kb < a.nk; ++kb, ++it) {
+          const int s = it % kTcStages;
+          const uint32_t ph = (it / kTcStages) & 1u;
+          if (!mbar_wait(full0 + 8 * s, ph, a.limit)) {
+            *err = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint64_t ad = sw128_kmajor_desc(smem_u32(sA + s * kTcABytes));
+          const uint64_t bd = sw128_kmajor_desc(smem_u32(sB + s * kTcBBytes));
+#pragma unroll
+          for (int ks = 0; ks < kTcK / 16; ++ks)  // 16 elements = 32 bytes per step along K
+            umma_f16kind(d, ad + 2 * ks, bd + 2 * ks, a.idesc, (kb | ks) != 0);
+          umma_commit(empty0 + 8 * s);
+        }
+        if (!ok) break;
+        umma_commit(accf0 + 8 * buf);
+      }
+      // every MMA this thread issued completes before the tensor memory is freed
+      umma_commit(drain);
+      mbar_wait(drain, 0, kSpinDefault);
+    }
+    __syncwarp();
+  } else {  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    const float c2 = *a.c2;
+    uint32_t tc = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      const bool ok = !*err && mbar_wait(accf0 + 8 * buf, (tc >> 1) & 1u, a.limit);
+      // the four epilogue warps take the same decision, so that none of them
+      // waits at a named barrier that another has left
+      if (epi_any(!ok)) {
+        *err = 1;
         break;
       }
       tc_fence_after();
-      const uint64_t ad = sw128_kmajor_desc(smem_u32(sA + s * kTcABytes));
-      const uint64_t bd = sw128_kmajor_desc(smem_u32(sB + s * kTcBBytes));
+      const int pt_vis = t / a.nqt;
+      const int64_t p0 = (int64_t)pt_vis * a.stride * kTcM;
+      const int q0 = (t % a.nqt) * kTcN;
+      const int64_t p = p0 + row;
+      const float xv = p < a.n ? __ldg(a.xn + p) : INFINITY;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTcN);
+      for (int c0 = 0; c0 < kTcN; c0 += 16) {
+        float v[16];
+        tmem_ld_x16(taddr + (uint32_t)c0, v);
+        if (a.pass == 1) {
 #pragma unroll
-      for (int ks = 0; ks < kTcK / 16; ++ks)  // 16 BF16 = 32 bytes per step along K
-        umma_bf16(tmem, ad + 2 * ks, bd + 2 * ks, (kb | ks) != 0);
-      umma_commit(empty0 + 8 * s);
-    }
-    umma_commit(done);
-  }
-  __syncwarp();
-
-  // ---- epilogue: lanes of TMEM are the tile's 128 points, columns its queries
-  const bool ok = mbar_wait(done, 0);
-  tc_fence_after();
-  const int row = warp * 32 + lane;
-  const int64_t p = p0 + row;
-  const float xv = (p < n) ? xn[p] : 0.0f;
-  for (int c0 = 0; c0 < kTcN; c0 += 16) {
-    float v[16];
-    tmem_ld_x16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (ok && p < n) {
+          for (int j = 0; j < 16; ++j) {
+            const int q = q0 + c0 + j;
+            v[j] = (p < a.n && q < a.nq) ? fmaf(c2, v[j], xv + __ldg(a.qn + q)) : INFINITY;
+          }
+          const float mn = warp_min16(v, lane);
+          const int q = q0 + c0 + (lane >> 1);
+          if ((lane & 1) == 0 && q < a.nq) a.gmin[(size_t)q * a.nunits + pt_vis * 4 + quarter] = mn;
+        } else if (p < a.n) {
+          // stage passing pairs per query column in shared memory (a global
+          // atomic per pair here would stall the warp for its round trip)
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int q = q0 + c0 + j;
-        if (q < nq) D[(size_t)q * n + p] = (xv + qn[q]) - 2.0f * v[j];
+          for (int j = 0; j < 16; ++j) {
+            const int c = c0 + j, q = q0 + c;
+            if (q < a.nq) {
+              const float D = fmaf(c2, v[j], xv + __ldg(a.qn + q));
+              if (D <= __ldg(a.cut + q)) {
+                const int slot = atomicAdd(&scnt[c], 1);
+                if (slot < kStage) {
+                  srow[c * kStage + slot] = (uint8_t)row;
+                } else {  // a crowded column: straight to the global list
+                  const int pos = atomicAdd(a.cnt + q, 1);
+                  if (pos < a.cap) a.cand[(size_t)q * a.cap + pos] = p;
+                }
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acce0 + 8 * buf);  // the accumulator is free for the next tile's MMAs
+      if (a.pass == 2) {
+        // flush: one global reservation per column with staged pairs
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        for (int c = threadIdx.x - 64; c < kTcN; c += 128) {
+          const int cnt_c = min(scnt[c], kStage);
+          if (cnt_c > 0) {
+            const int q = q0 + c;
+            const int base = atomicAdd(a.cnt + q, cnt_c);
+            for (int i = 0; i < cnt_c; ++i)
+              if (base + i < a.cap) a.cand[(size_t)q * a.cap + base + i] = p0 + srow[c * kStage + i];
+          }
+          scnt[c] = 0;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
       }
     }
   }
-  if (!ok) *cta_err = 1;
-  tc_fence_before();
+
   __syncthreads();
-  if (*cta_err) {
-    if (threadIdx.x == 0) atomicExch(status, kStatusTimeout);
-    // let the copies this CTA issued land before its shared memory is released
+  if (*err) {
+    if (threadIdx.x == 0) atomicExch(a.status, kStatusTimeout);
+    // the copies this CTA issued land before its shared memory is released
     if (warp == 0 && lane == 0)
-      for (int kb = (issued > kTcStages ? issued - kTcStages : 0); kb < issued; ++kb)
-        mbar_wait(full0 + 8 * (kb % kTcStages), (uint32_t)(kb / kTcStages) & 1u);
+      for (uint32_t it = (issued > kTcStages ? issued - kTcStages : 0); it < issued; ++it)
+        mbar_wait(full0 + 8 * (it % kTcStages), (it / kTcStages) & 1u, kSpinDefault);
   }
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
   }
 }
 
-// ---- operand preparation
+// ---- pass 1 -> pass 2: the cut of each query
+
+// cut_q = tau_q + 2 E_q (plus a few units of roundoff), tau_q the k-th
+// smallest group minimum of pass 1; +inf when there are fewer than k groups.
+// Also zeroes the query's candidate count for pass 2.
+constexpr int kCutNT = 256;
+
+__global__ void __launch_bounds__(kCutNT) screen_cut_kernel(const float* __restrict__ gmin, int nunits, int k, int m,
+                                                            const float* __restrict__ qn,
+                                                            const unsigned* __restrict__ xn_max_bits,
+                                                            float c_cross, float c_square, float* __restrict__ cut,
+                                                            int* __restrict__ cnt) {
+  __shared__ uint32_t hist[kHistBins];
+  __shared__ uint32_t buf[kSelCap];
+  __shared__ BlockScratch<kCutNT> bs;
+  __shared__ SelectShared ss;
+  const int q = blockIdx.x;
+  float tau = INFINITY;
+  if (nunits >= k) {
+    const float* g = gmin + (size_t)q * nunits;
+    for (int i = threadIdx.x; i < kHistBins; i += kCutNT) hist[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nunits; i += kCutNT) atomicAdd(&hist[f2key(g[i]) >> 20], 1u);
+    __syncthreads();
+    select_smallest<kCutNT>([&](int i) { return f2key(g[i]); }, nunits, k, hist, buf, ss, bs);
+    tau = key2f(buf[k - 1]);
+  }
+  if (threadIdx.x == 0) {
+    float c = INFINITY;
+    if (isfinite(tau)) {
+      // FP32 arithmetic on non-negative terms: a few units of roundoff,
+      // covered by the factor 1.001 (the coefficients carry their own margins)
+      const float u = 1.0f / 16777216.0f;
+      const float gm = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);  // the norms' FP32 sums
+      const float xmax = sqrtf(__uint_as_float(*xn_max_bits) * (1.0f + gm));
+      const float qq = sqrtf(qn[q] * (1.0f + gm));
+      const float E = 1.001f * (c_cross * xmax * qq + c_square * (xmax + qq) * (xmax + qq));
+      const float x = tau + 2.0f * E;
+      c = x + 8.0f * u * fabsf(x) + 1e-30f;
+    }
+    cut[q] = c;
+    cnt[q] = 0;
+  }
+}
+
+// ---- operands
 
 // Column sums of X (any fixed vector works as the centre; this one keeps the
 // centred values small).
@@ -243,32 +467,71 @@ static __global__ void scale_kernel(float* v, int m, float f) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) v[j] *= f;
 }
 
-// Rows of the screen operand: [hi | hi | lo] (dataset side, second = false)
-// or [hi | lo | hi] (query side, second = true) of x - mu, each Kp wide and
-// zero padded; norms[r] = ||x - mu||^2 (FP32), max_bits its largest value.
-static __global__ void split_rows_kernel(const float* __restrict__ X, int64_t rows, int64_t rows_pad, int m, int Kp,
-                                         const float* __restrict__ mu, bool query_side, uint16_t* __restrict__ out,
+// Largest |x - mu| over rows (float bits of a non-negative value, atomicMax).
+static __global__ void centred_absmax_kernel(const float* __restrict__ X, int64_t rows, int m,
+                                             const float* __restrict__ mu, unsigned* max_bits) {
+  unsigned mx = 0;
+  const size_t count = (size_t)rows * (size_t)m;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+    mx = max(mx, __float_as_uint(fabsf(__ldg(X + e) - mu[e % m])));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(max_bits, mx);
+}
+
+// Power-of-two exponent that brings the largest |value| M into [2^14, 2^15)
+// (FP16's largest finite value is 65504): 0 for M = 0.
+__device__ __forceinline__ int f16_exponent(unsigned max_bits) {
+  const float M = __uint_as_float(max_bits);
+  if (!(M > 0.0f) || !isfinite(M)) return 0;
+  return max(-120, min(120, 14 - ilogbf(M)));
+}
+
+// -2 / (product of the operand scales): the coefficient of the accumulator in
+// the screened distance.
+static __global__ void screen_coeff_kernel(int kind, const unsigned* xmax_bits, const unsigned* qmax_bits,
+                                           float* c2) {
+  if (kind == kKindF16)
+    *c2 = ldexpf(-2.0f, -(f16_exponent(*xmax_bits) + f16_exponent(*qmax_bits)));
+  else
+    *c2 = -2.0f;
+}
+
+// Rows of a screen operand from x - mu, each part Kp wide and zero padded:
+//   F16:    [fp16(2^e (x - mu))], e from the largest |x - mu| of the side;
+//   BF16:   [bf16(x - mu)];
+//   BF16X3: [hi | hi | lo] (data side) or [hi | lo | hi] (query side).
+// norms[r] = ||x - mu||^2 (FP32), max_bits their largest value.
+static __global__ void split_rows_kernel(int kind, const float* __restrict__ X, int64_t rows, int64_t rows_pad, int m,
+                                         int Kp, const float* __restrict__ mu, bool query_side,
+                                         const unsigned* __restrict__ absmax_bits, uint16_t* __restrict__ out,
                                          float* __restrict__ norms, unsigned* max_bits) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int parts = kind == kKindBF16x3 ? 3 : 1;
+  const int e = kind == kKindF16 ? f16_exponent(*absmax_bits) : 0;
   unsigned mx = 0;
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows_pad; r += warps) {
-    uint16_t* o = out + (size_t)r * 3 * Kp;
+    uint16_t* o = out + (size_t)r * parts * Kp;
     float s = 0.0f;
     for (int j = lane; j < Kp; j += 32) {
-      uint16_t hb = 0, lb = 0;
+      float xc = 0.0f;
       if (r < rows && j < m) {
-        const float xc = __ldg(X + (size_t)r * m + j) - mu[j];
-        const __nv_bfloat16 h = __float2bfloat16_rn(xc);
-        const float hf = __bfloat162float(h);
-        const __nv_bfloat16 l = __float2bfloat16_rn(xc - hf);
-        hb = __bfloat16_as_ushort(h);
-        lb = __bfloat16_as_ushort(l);
+        xc = __ldg(X + (size_t)r * m + j) - mu[j];
         s = fmaf(xc, xc, s);
       }
-      o[j] = hb;
-      o[Kp + j] = query_side ? lb : hb;
-      o[2 * Kp + j] = query_side ? hb : lb;
+      if (kind == kKindF16) {
+        o[j] = __half_as_ushort(__float2half_rn(ldexpf(xc, e)));
+      } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(xc);
+        const uint16_t hb = __bfloat16_as_ushort(h);
+        o[j] = hb;
+        if (kind == kKindBF16x3) {
+          const uint16_t lb = __bfloat16_as_ushort(__float2bfloat16_rn(xc - __bfloat162float(h)));
+          o[Kp + j] = query_side ? lb : hb;
+          o[2 * Kp + j] = query_side ? hb : lb;
+        }
+      }
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
@@ -305,9 +568,9 @@ static knn_status get_encoder(EncodeTiled* out) {
   return KNN_OK;
 }
 
-// 2-D BF16 tensor map over rows x Kt (row pitch Kt elements), box 64 x box_rows,
-// 128-byte swizzle; rows beyond the tensor read as zero.
-static knn_status make_map(CUtensorMap* map, const void* base, int64_t rows, int Kt, int box_rows) {
+// 2-D 16-bit tensor map over rows x Kt (row pitch Kt elements), box 64 x
+// box_rows, 128-byte swizzle. Every tile the kernel loads lies inside rows.
+static knn_status make_map(CUtensorMap* map, const void* base, int64_t rows, int Kt, int box_rows, bool bf16) {
   EncodeTiled enc;
   knn_status s = get_encoder(&enc);
   if (s != KNN_OK) return s;
@@ -315,9 +578,9 @@ static knn_status make_map(CUtensorMap* map, const void* base, int64_t rows, int
   cuuint64_t strides[1] = {(cuuint64_t)Kt * 2};
   cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return KNN_ECUDA;
@@ -326,59 +589,109 @@ static knn_status make_map(CUtensorMap* map, const void* base, int64_t rows, int
 }
 
 static size_t screen_smem_bytes() {
-  return 1024 + (size_t)kTcStages * (kTcABytes + kTcBBytes) + (2 * kTcStages + 1) * 8 + 16;
+  return 1024 + (size_t)kTcStages * (kTcABytes + kTcBBytes) + (2 * kTcStages + 5) * 8 + 16 + kTcN * 4 +
+         kTcN * kStage;
 }
 
-// Builds the dataset's screen operand (called by knn_dataset_create).
-knn_status build_screen_operand(knn_dataset* ds, cudaStream_t stream) {
+static int kind_of_screen(int32_t screen) {
+  return screen == KNN_SCREEN_F16 ? kKindF16 : (screen == KNN_SCREEN_BF16 ? kKindBF16 : kKindBF16x3);
+}
+static int parts_of(int kind) { return kind == kKindBF16x3 ? 3 : 1; }
+
+static uint16_t* operand_of(const knn_dataset* ds, int kind) {
+  return kind == kKindF16 ? ds->screen16 : (kind == kKindBF16 ? ds->screenb : ds->screenA);
+}
+
+// Builds the dataset's screen operands named in `copies` (KNN_COPY_SCREEN*;
+// called by knn_dataset_create): the column mean, the centred norms and
+// their largest value once, then each operand.
+knn_status build_screen_operand(knn_dataset* ds, int32_t copies, cudaStream_t stream) {
   const int64_t n = ds->n;
   const int m = ds->m;
   ds->Kp = (m + kTcK - 1) / kTcK * kTcK;
   const size_t rows_pad = (size_t)((n + kTcM - 1) / kTcM) * kTcM;
-  knn_status s = cuda_check(cudaMalloc(&ds->screenA, rows_pad * 3 * (size_t)ds->Kp * 2), "cudaMalloc(screen operand)");
-  if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->mu, (size_t)m * 4), "cudaMalloc(mu)");
+  knn_status s = cuda_check(cudaMalloc(&ds->mu, (size_t)m * 4), "cudaMalloc(mu)");
   if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->xcn, (size_t)n * 4), "cudaMalloc(norms)");
-  if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->xcn_max, 4), "cudaMalloc(norm max)");
+  if (s == KNN_OK) s = cuda_check(cudaMalloc(&ds->xcn_max, 8), "cudaMalloc(norm max)");
   if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->mu, 0, (size_t)m * 4, stream), "memset");
-  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->xcn_max, 0, 4, stream), "memset");
-  if (s != KNN_OK) return s;
+  if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->xcn_max, 0, 8, stream), "memset");
   DeviceInfo di;
-  s = device_info(&di);
+  if (s == KNN_OK) s = device_info(&di);
   if (s != KNN_OK) return s;
   column_sums_kernel<<<di.sms * 4, 256, 0, stream>>>(ds->X, n, m, ds->mu);
   scale_kernel<<<(m + 255) / 256, 256, 0, stream>>>(ds->mu, m, 1.0f / (float)n);
-  split_rows_kernel<<<di.sms * 8, 256, 0, stream>>>(ds->X, n, (int64_t)rows_pad, m, ds->Kp, ds->mu, false,
-                                                     ds->screenA, ds->xcn, ds->xcn_max);
-  return cuda_check(cudaGetLastError(), "screen operand kernels");
+  // xcn_max[1]: largest |x - mu| (the FP16 operand's scale)
+  centred_absmax_kernel<<<di.sms * 8, 256, 0, stream>>>(ds->X, n, m, ds->mu, ds->xcn_max + 1);
+  s = cuda_check(cudaGetLastError(), "screen operand kernels");
+  struct Want {
+    int32_t flag;
+    int kind;
+    uint16_t** dst;
+  } wants[3] = {{KNN_COPY_SCREEN, kKindBF16x3, &ds->screenA},
+                {KNN_COPY_SCREEN_F16, kKindF16, &ds->screen16},
+                {KNN_COPY_SCREEN_BF16, kKindBF16, &ds->screenb}};
+  bool norms = false;
+  for (const Want& w : wants) {
+    if (s != KNN_OK || !(copies & w.flag)) continue;
+    s = cuda_check(cudaMalloc(w.dst, rows_pad * parts_of(w.kind) * (size_t)ds->Kp * 2), "cudaMalloc(screen operand)");
+    if (s != KNN_OK) break;
+    split_rows_kernel<<<di.sms * 8, 256, 0, stream>>>(w.kind, ds->X, n, (int64_t)rows_pad, m, ds->Kp, ds->mu, false,
+                                                       ds->xcn_max + 1, *w.dst, ds->xcn,
+                                                       norms ? nullptr : ds->xcn_max);
+    norms = true;
+    s = cuda_check(cudaGetLastError(), "screen operand kernels");
+  }
+  return s;
 }
 
 struct TcCarve {
   uint16_t* B;
   float* qn;
-  float* D;
+  unsigned* qmax;  // [1] largest |q - mu| of the batch
+  float* c2;
+  float* gmin;
+  float* cut;
+  int* cnt;
   int64_t* cand;
 };
 
-static size_t carve_tc(Carve& cv, int64_t n, int32_t nq, int Kp, TcCarve* out) {
+static size_t carve_tc(Carve& cv, int64_t n, int32_t nq, int Kt, TcCarve* out) {
   TcCarve c;
   const size_t nq_pad = (size_t)((nq + kTcN - 1) / kTcN) * kTcN;
-  c.B = cv.take<uint16_t>(nq_pad * 3 * (size_t)Kp);
+  const size_t npt = (size_t)((n + kTcM - 1) / kTcM);
+  c.B = cv.take<uint16_t>(nq_pad * (size_t)Kt);
   c.qn = cv.take<float>(nq_pad);
-  c.D = cv.take<float>((size_t)nq * (size_t)n);
-  c.cand = cv.take<int64_t>((size_t)nq * kExactCandTc);
+  c.qmax = cv.take<unsigned>(1);
+  c.c2 = cv.take<float>(1);
+  c.gmin = cv.take<float>((size_t)nq * 4 * npt);
+  c.cut = cv.take<float>((size_t)nq);
+  c.cnt = cv.take<int>((size_t)nq);
+  c.cand = cv.take<int64_t>((size_t)nq * kScreenCap);
   if (out) *out = c;
   return cv.off;
 }
 
-size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq) {
+size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq, int32_t screen) {
   Carve cv;
-  return carve_tc(cv, n, nq, (m + kTcK - 1) / kTcK * kTcK, nullptr) + 256;
+  const int Kp = (m + kTcK - 1) / kTcK * kTcK;
+  return carve_tc(cv, n, nq, parts_of(kind_of_screen(screen)) * Kp, nullptr) + 256;
 }
 
-knn_status exact_tc(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k, int64_t* out_idx,
+// Point tiles skipped between the tiles pass 1 visits: the k-th smallest of
+// the visited groups' minima then lies near the (s k)-th smallest screened
+// value, so about s k points (plus the screen's margin) become candidates.
+static int pass1_stride(int64_t npt, int k) {
+  int s = std::max(1, std::min(16, 64 / k));
+  while (s > 1 && 4 * ((npt + s - 1) / s) < 4 * (int64_t)k) --s;
+  return s;
+}
+
+knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32_t nq, int32_t k, int64_t* out_idx,
                     double* out_dist, void* workspace, size_t workspace_bytes, cudaStream_t stream) {
-  if (!ds->screenA) {
-    set_error("knn_exact_ds: the dataset was created without the tensor-core screen operand");
+  const int kind = kind_of_screen(screen);
+  const uint16_t* A = operand_of(ds, kind);
+  if (!A) {
+    set_error("knn_exact_ds: the dataset was created without this screen's operand (KNN_COPY_SCREEN*)");
     return KNN_EINVAL;
   }
   DeviceInfo di;
@@ -389,53 +702,111 @@ knn_status exact_tc(const knn_dataset* ds, const float* Q, int32_t nq, int32_t k
     return KNN_EUNSUPPORTED;
   }
   const int64_t n = ds->n;
-  const int m = ds->m, Kp = ds->Kp, Kt = 3 * Kp;
-  const size_t need = exact_tc_workspace(n, m, nq);
+  const int m = ds->m, Kp = ds->Kp, Kt = parts_of(kind) * Kp;
+  const size_t need = exact_tc_workspace(n, m, nq, screen);
   Workspace ws;
   s = ws.acquire(workspace, workspace_bytes, need, stream);
   if (s != KNN_OK) return s;
   Carve cv;
   cv.base = reinterpret_cast<uint8_t*>(((uintptr_t)ws.ptr + 255) & ~uintptr_t(255));
   TcCarve c;
-  carve_tc(cv, n, nq, Kp, &c);
+  carve_tc(cv, n, nq, Kt, &c);
   const int64_t nq_pad = (int64_t)((nq + kTcN - 1) / kTcN) * kTcN;
-  split_rows_kernel<<<(int)std::min<int64_t>((nq_pad + 7) / 8, (int64_t)di.sms * 8), 256, 0, stream>>>(
-      Q, nq, nq_pad, m, Kp, ds->mu, true, c.B, c.qn, nullptr);
-  s = cuda_check(cudaGetLastError(), "query split kernel");
+  const int64_t npt = (n + kTcM - 1) / kTcM;
+  const int nqt = (int)(nq_pad / kTcN);
+
+  // query operand, norms and the accumulator's coefficient
+  s = cuda_check(cudaMemsetAsync(c.qmax, 0, 4, stream), "memset");
+  if (s == KNN_OK) {
+    if (kind == kKindF16)
+      centred_absmax_kernel<<<(int)std::min<int64_t>(((int64_t)nq * m + 255) / 256, (int64_t)di.sms * 8), 256, 0,
+                              stream>>>(Q, nq, m, ds->mu, c.qmax);
+    split_rows_kernel<<<(int)std::min<int64_t>((nq_pad + 7) / 8, (int64_t)di.sms * 8), 256, 0, stream>>>(
+        kind, Q, nq, nq_pad, m, Kp, ds->mu, true, c.qmax, c.B, c.qn, nullptr);
+    screen_coeff_kernel<<<1, 1, 0, stream>>>(kind, ds->xcn_max + 1, c.qmax, c.c2);
+    s = cuda_check(cudaGetLastError(), "query operand kernels");
+  }
   CUtensorMap mapA, mapB;
-  if (s == KNN_OK) s = make_map(&mapA, ds->screenA, (n + kTcM - 1) / kTcM * kTcM, Kt, kTcM);
-  if (s == KNN_OK) s = make_map(&mapB, c.B, nq_pad, Kt, kTcN);
+  const bool bf16 = kind != kKindF16;
+  if (s == KNN_OK) s = make_map(&mapA, A, npt * kTcM, Kt, kTcM, bf16);
+  if (s == KNN_OK) s = make_map(&mapB, c.B, nq_pad, Kt, kTcN, bf16);
   int* status = nullptr;
   if (s == KNN_OK) s = device_status_ptr(&status);
-  if (s == KNN_OK) {
-    const size_t smem = screen_smem_bytes();
+  const size_t smem = screen_smem_bytes();
+  if (s == KNN_OK)
     s = cuda_check(cudaFuncSetAttribute(screen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                    "cudaFuncSetAttribute(screen_tc)");
-    if (s == KNN_OK) {
-      dim3 grid((unsigned)(nq_pad / kTcN), (unsigned)((n + kTcM - 1) / kTcM));
-      screen_tc_kernel<<<grid, kTcThreads, smem, stream>>>(mapA, mapB, n, nq, Kt, ds->xcn, c.qn, c.D, status);
-      s = cuda_check(cudaGetLastError(), "screen_tc_kernel launch");
-    }
+  ScreenArgs a{};
+  a.n = n;
+  a.nq = nq;
+  a.nk = Kt / kTcK;
+  a.nqt = nqt;
+  a.idesc = idesc_f16kind(bf16);
+  a.limit = g_wait_limit.load();
+  a.xn = ds->xcn;
+  a.qn = c.qn;
+  a.c2 = c.c2;
+  a.gmin = c.gmin;
+  a.cut = c.cut;
+  a.cnt = c.cnt;
+  a.cand = c.cand;
+  a.cap = kScreenCap;
+  a.status = status;
+
+  // pass 1: group minima over every s-th point tile (skipped when every
+  // point fits the candidate list: the cut is then +inf)
+  const bool pass1 = n > kScreenCap;
+  const int stride = pass1 ? pass1_stride(npt, k) : 1;
+  const int64_t nvis = (npt + stride - 1) / stride;
+  a.nunits = pass1 ? (int)(4 * nvis) : 0;
+  if (s == KNN_OK && pass1) {
+    a.pass = 1;
+    a.stride = stride;
+    a.ntiles = (int)(nvis * nqt);
+    screen_tc_kernel<<<std::min(a.ntiles, di.sms), kTcThreads, smem, stream>>>(mapA, mapB, a);
+    s = cuda_check(cudaGetLastError(), "screen_tc_kernel launch (pass 1)");
   }
   if (s == KNN_OK) {
-    // Error bound of a screened value (u = 2^-24): the K-concatenated product
-    // misses at most 3.1 * 2^-18 sum|xc||qc| from the split, and its FP32
-    // tensor-core accumulation over Kt terms is bounded by (Kt + 16) 2^-22
-    // sum|terms| (two units of the last place per term, covering truncating
-    // adders); sum|xc||qc| <= ||xc|| ||qc||. The centred norms are FP32 sums
-    // over m terms (gamma_m), and the final additions and the centring cost a
-    // few units of roundoff of (||xc|| + ||qc||)^2. A factor 1.5 covers
+    // Error bound of a screened value (u = 2^-24): the operands' rounding
+    // (F16: (2 u16 + u16^2) sum|xc qc|, u16 = 2^-11, plus the subnormal
+    // spacing of the scaled values, below 2^-30 ||xc|| ||qc||; BF16: u16 =
+    // 2^-8; BF16x3: the split residuals, 3.1 2^-18 sum|xc qc|), the FP32
+    // tensor-core accumulation over Kt terms ((Kt + 16) 2^-22 sum|terms|:
+    // two units of the last place per term, covering truncating adders), and
+    // the norms' FP32 sums (gamma_m) with the final additions (a few units of
+    // (||xc|| + ||qc||)^2); sum|xc qc| <= ||xc|| ||qc||. A factor 1.5 covers
     // second-order terms.
     const double u = 1.0 / 16777216.0;
     const double gacc = (double)(Kt + 16) * 4.0 * u;
+    double prod;
+    if (kind == kKindF16) prod = 2.0 * std::ldexp(1.0, -11) + std::ldexp(1.0, -22) + std::ldexp(1.0, -30);
+    else if (kind == kKindBF16) prod = 2.0 * std::ldexp(1.0, -8) + std::ldexp(1.0, -16);
+    else prod = 3.1 * 64.0 * u;
     const double gm = (double)(m + 2) * u / (1.0 - (double)(m + 2) * u);
-    const double c_cross = 1.5 * 2.0 * (gacc + 3.1 * 64.0 * u) * 1.01;
+    const double c_cross = 1.5 * 2.0 * (gacc + prod) * 1.01;
     const double c_square = 1.5 * (gm + 6.0 * u);
-    s = launch_screen_select(c.D, n, nq, m, k, c.qn, ds->xcn_max, c_cross, c_square, ds->X, Q, c.cand, stream);
+    screen_cut_kernel<<<nq, kCutNT, 0, stream>>>(c.gmin, a.nunits, k, m, c.qn, ds->xcn_max, (float)c_cross,
+                                                 (float)c_square, c.cut, c.cnt);
+    s = cuda_check(cudaGetLastError(), "screen_cut_kernel launch");
   }
-  if (s == KNN_OK) s = launch_rerank(ds->X, n, m, Q, nq, c.cand, kExactCandTc, k, out_idx, out_dist, stream);
+  if (s == KNN_OK) {  // pass 2: candidates
+    a.pass = 2;
+    a.stride = 1;
+    a.ntiles = (int)(npt * nqt);
+    screen_tc_kernel<<<std::min(a.ntiles, di.sms), kTcThreads, smem, stream>>>(mapA, mapB, a);
+    s = cuda_check(cudaGetLastError(), "screen_tc_kernel launch (pass 2)");
+  }
+  if (s == KNN_OK)
+    s = launch_refine(ds->X, n, m, Q, nq, c.cand, kScreenCap, c.cnt, k, out_idx, out_dist, stream, KNN_METRIC_L2SQ);
   ws.release();
   return s;
 }
 
 }  // namespace knn
+
+// Tries of the tensor-core kernels' pipeline waits before they give up.
+extern "C" knn_status knn_debug_wait_limit(int64_t tries) {
+  knn::clear_error();
+  knn::g_wait_limit.store(tries < 0 ? knn::kSpinDefault : (uint32_t)std::min<int64_t>(tries, 0xFFFFFFFFll));
+  return KNN_OK;
+}

@@ -23,7 +23,8 @@ _lib = None
 BOUNDS = {"footnote": 0, "lemma": 1, "exp": 2}
 STORAGE = {"f32": 0, "bf16": 1, "fp8": 2}
 COPY_SCREEN = 1 << 3
-SCREENS = {"f32": 0, "bf16x3": 1}
+COPY_SCREENS = {"screen": 1 << 3, "screen_f16": 1 << 4, "screen_bf16": 1 << 5}
+SCREENS = {"f32": 0, "bf16x3": 1, "f16": 2, "bf16": 3}
 ACTIVE, ELIMINATED, ACCEPTED = 0, 1, 2
 MAX_KH = 1024  # largest k + h (candidate set size) the library accepts
 FULL_MASK = (1 << 64) - 1
@@ -60,6 +61,7 @@ _SIGS = {
     "knn_exact_ds_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32]),
     "knn_exact_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "knn_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
+    "knn_debug_wait_limit": (C.c_int, [C.c_int64]),
     "knn_phase_clocks": (C.c_int, [C.POINTER(C.c_uint64), C.c_int32]),
     "knn_adaptive_ds_multi_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32, C.POINTER(Opts)]),
     "knn_adaptive_ds_multi": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_double, C.c_uint64,
@@ -201,7 +203,7 @@ class Dataset:
     def __init__(self, X: torch.Tensor, copies=("bf16", "fp8"), stream=None):
         mask = 0
         for c in copies:
-            mask |= COPY_SCREEN if c == "screen" else 1 << STORAGE[c]
+            mask |= COPY_SCREENS[c] if c in COPY_SCREENS else 1 << STORAGE[c]
         self.X = X
         self.n, self.m = X.shape
         self.copies = tuple(copies)
@@ -341,6 +343,12 @@ def exact(X: torch.Tensor, Q: torch.Tensor, k: int, workspace: torch.Tensor | No
             _dev(dist, "dist", torch.float64), ws_ptr, ws_bytes, _stream(stream))
     _check(rc)
     return idx, dist
+
+
+def debug_wait_limit(tries: int) -> None:
+    """Test hook: the tensor-core kernels' pipeline waits give up after
+    `tries` polls (negative: the default) -- knn_debug_wait_limit."""
+    _check(lib().knn_debug_wait_limit(int(tries)))
 
 
 def device_status() -> int:
