@@ -197,7 +197,7 @@ def run_ours(args, rank, world, local_rank):
     Hd = torch.from_numpy(H).to(dev)
     stream = torch.cuda.current_stream()
 
-    ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen"))
+    ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen", "screen_f16", "screen_bf16"))
 
     tuned = {}
 
@@ -264,19 +264,26 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- dominant kernel alone (the round-loop kernel; the range is cached in the dataset)
     def kernel_alone(storage, best_s, reps=3):
+        """Median time of one knn_adaptive_ds call, and the library's own CUDA
+        events (on this stream) around its two kernels: the point-major
+        round-0 pass and the round-loop kernel (mean per call)."""
         ka = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         o = None
         ws = torch.empty(knn.adaptive_workspace_size(n, m, nq, k, knn.make_opts(k, **opts_of(best_s))),
                          dtype=torch.uint8, device=dev)
+        knn.kernel_timing(True)
+        knn.kernel_times(reset=True)
         for a_, b_ in ka:
             a_.record(stream)
             o = ds.adaptive(Qd, k, w["delta"], 0, storage=storage, qid_base=qid_base, out=o, workspace=ws,
                             **opts_of(best_s))
             b_.record(stream)
         torch.cuda.synchronize()
-        return statistics.median(a_.elapsed_time(b_) for a_, b_ in ka), o
+        r0_ms, loop_ms = knn.kernel_times(reset=True)
+        knn.kernel_timing(False)
+        return statistics.median(a_.elapsed_time(b_) for a_, b_ in ka), o, r0_ms / reps, loop_ms / reps
 
-    kern_ms, out = kernel_alone("f32", best)
+    kern_ms, out, r0_kern_ms, loop_kern_ms = kernel_alone("f32", best)
     evals = int(out["evals"].sum().item())
     rounds = out["rounds"].cpu().numpy()
     # The call is two kernels: the point-major round-0 pass (streams X once,
@@ -289,11 +296,19 @@ def run_ours(args, rank, world, local_rank):
     grid = torch.cuda.get_device_properties(dev).multi_processor_count * (1024 // best["threads"])
     chunk = min(nq, max((1 << 30) // (4 * n), grid)) if r0_evals else nq
     launches_per_step = -(-nq // chunk) * (2 if r0_evals else 1) + 1
-    alg_bytes = (4 * n * m + 2 * 4 * nq * n if r0_evals else 0) + 4 * (evals - r0_evals) + 4 * nq * m
+    # Algorithmic bytes (element bytes per coordinate evaluation): the round
+    # loop -- the dominant kernel -- reads 4 B per evaluation after round 0
+    # and the round-0 sums (4 B per pair); the whole call moves 4 B per
+    # evaluation. The builder's byte count of the call (X streamed once by the
+    # round-0 pass + sums written and read + later evaluations + query rows)
+    # stays beside it.
+    alg_bytes = 4 * (evals - r0_evals) + (4 * nq * n if r0_evals else 0)
+    alg_bytes_call = 4 * evals
+    alg_bytes_builder = (4 * n * m + 2 * 4 * nq * n if r0_evals else 0) + 4 * (evals - r0_evals) + 4 * nq * m
     hbm, peak_kind = peaks()
-    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    achieved = alg_bytes / (loop_kern_ms / 1e3) / 1e9
     cfg_now = {"c_alpha": chosen, "B0": B0, "B": B, "grow": grow, "threads": best["threads"], "nq": nq}
-    traffic = (TRAFFIC_CAPTURE["bytes"] if kernel_sources_sha1() == TRAFFIC_CAPTURE["sha1"]
+    traffic = (TRAFFIC_CAPTURE["rounds_bytes"] if kernel_sources_sha1() == TRAFFIC_CAPTURE["sha1"]
                and cfg_now == TRAFFIC_CAPTURE["config"] else None)
     sector_gbs = 32 * evals / (kern_ms / 1e3) / 1e9
 
@@ -317,10 +332,16 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         return max_over_ranks(e0.elapsed_time(e1) / steps), ei
 
-    ex_steps = max(2, min(args.steps, 5))
-    exact_ms, ei_tc = time_exact("bf16x3", ex_steps)
+    ex_steps = max(3, min(args.steps, 10))
+    exact_screens = {}
+    for screen in ("f16", "bf16", "bf16x3"):
+        ms_e, ei_e = time_exact(screen, ex_steps)
+        exact_screens[screen] = {"queries_per_s": round(world * nq / (ms_e / 1e3), 3), "ms_per_batch": round(ms_e, 4),
+                                 "agrees_with_simt_path": bool(torch.equal(ei_e, ti))}
+    exact_screen = min(exact_screens, key=lambda sc: exact_screens[sc]["ms_per_batch"])
+    exact_ms = exact_screens[exact_screen]["ms_per_batch"]
+    exact_agree = all(v["agrees_with_simt_path"] for v in exact_screens.values())
     exact_simt_ms, _ = time_exact("f32", 2)
-    exact_agree = bool(torch.equal(ei_tc, ti))
 
     # ---- stored copies (BF16, FP8 e4m3 + per-row scale): same step, calibrated separately
     variants = {}
@@ -339,7 +360,7 @@ def run_ours(args, rank, world, local_rank):
         v1.record(stream)
         torch.cuda.synchronize()
         ms_s = max_over_ranks(v0.elapsed_time(v1) / vsteps)
-        kms_s, o_s = kernel_alone(storage, best_s)
+        kms_s, o_s, _, _ = kernel_alone(storage, best_s)
         ev_s = int(o_s["evals"].sum().item())
         elem = 2 if storage == "bf16" else 1
         variants[storage] = {
@@ -351,13 +372,16 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- shared coordinates (both counter masks zero): column-permuted copies, contiguous row prefixes
     shared = {}
+    shared_best = {}
     ds.share(0, copies=("f32", "bf16", "fp8"))
+    ds._shared_seed, ds._shared = 0, ("f32", "bf16", "fp8")
     SH = dict(share_points=True, share_queries=True)
     for storage in ("f32", "bf16", "fp8"):
         t = runtime.autotune(ds, Hd, k, w["delta"], storage=storage, target=RECALL_TARGET, margin=0.0005,
                              c_grid=[args.c_alpha] if args.c_alpha else C_GRID, use_cache=False, extra=SH,
                              cache=os.path.join(tempfile.gettempdir(), f"knn_bench_tune_sh_{os.getpid()}.json"))
         b = t["best"]
+        shared_best[storage] = b
         o_sh = dict(opts_of(b), **SH)
         step = runtime.GraphStep(ds, nq, k, w["delta"], 0, storage=storage, qid_base=qid_base, **o_sh)
         for _ in range(2):
@@ -379,6 +403,45 @@ def run_ours(args, rank, world, local_rank):
             "recall": round(recall_of(ri_s.cpu().numpy(), rd_s.cpu().numpy(), ti_np, td_np), 6),
             "tuned": b, "coord_evals_fraction": round(ev_s / (nq * n * m), 6),
             "alg_gbs_step": round(elem * ev_s / (ms_s / 1e3) / 1e9, 2)}
+
+    # ---- serving: requests of 1-256 queries (k = 10) from the batch's pool
+    # arrive as a Poisson process and are continuously batched onto the GPU
+    # (serve.Server: stream slots, admission by device-state bytes) in the
+    # served form -- shared coordinates over the BF16 copy -- at half and at
+    # one and a half times the batched rate of that form; latency per request
+    # from arrival to results on the host
+    serving = {}
+    try:
+        if world > 1:
+            raise RuntimeError("reported by single-GPU runs only")
+        from paper_1902_09465_gb300 import serve
+        b = shared_best["bf16"]
+        scfg = serve.DatasetConfig(storage="bf16", share=True, method="adaptive", c_alpha=b["c_alpha"], B0=b["B0"],
+                                   B=b["B"], grow=b["grow"], threads=b["threads"])
+        cap_qps = shared["bf16"]["queries_per_s"]
+        warm = serve.Server([ds], [scfg], slots=4, mem_budget=8 << 30)
+        warm.run(serve.poisson_requests(200.0, 0.05, [Q], max_queries=64, k_range=(k, k), seed=5)[:6])
+        for name, frac in (("half_load", 0.5), ("overload", 1.5)):
+            rate = frac * cap_qps / 128.5   # mean request: 128.5 queries
+            arrivals = serve.poisson_requests(rate, args.serve_seconds_bench, [Q], max_queries=256, k_range=(k, k),
+                                              seed=21 + int(10 * frac))
+            srv = serve.Server([ds], [scfg], slots=4, mem_budget=8 << 30)
+            torch.cuda.synchronize()
+            done = srv.run(arrivals, timeout_s=120)
+            st = serve.latency_stats(done)
+            hit = tot = 0
+            for r in done[:12]:   # recall of sampled requests against the exact method
+                ti_r, td_r = ds.exact(r.Q.to(dev), k)
+                hit += recall_of(r.idx.numpy(), r.dist.numpy(), ti_r.cpu().numpy(), td_r.cpu().numpy()) * r.Q.shape[0]
+                tot += r.Q.shape[0]
+            serving[name] = {"offered_queries_per_s": round(frac * cap_qps, 1),
+                             "served_queries_per_s": round(st["queries_per_s"], 1), "requests": st["requests"],
+                             "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                             "mean_batch_queries": round(float(np.mean([r.batch_size for r in done])), 1),
+                             "launches": srv.launches, "recall_sampled": round(hit / max(tot, 1), 6)}
+        serving["form"] = "shared coordinates over the BF16 copy, " + json.dumps(scfg.__dict__)
+    except Exception as exc:  # noqa: BLE001 -- reported, not hidden
+        serving = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     # ---- block samples (a draw reads one 32-byte block: 8 FP32 / 16 BF16 coordinates)
     blocks = {}
@@ -443,6 +506,21 @@ def run_ours(args, rank, world, local_rank):
     except Exception as exc:  # noqa: BLE001 -- reported, not hidden
         without_replacement = {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
+    # ---- traced runs of a few queries of the batch (alone, same Philox query
+    # ids), replayed by the oracle in the CPU-baseline leg: errors of the
+    # estimates against FP64 and the near-threshold decisions
+    trace_q = [0, nq // 3, (2 * nq) // 3, nq - 1]
+    traces = {}
+    for storage, b_s in (("f32", best), ("bf16", tuned["bf16"]["best"]), ("fp8", tuned["fp8"]["best"])):
+        rows_t = []
+        for q in trace_q:
+            r = ds.adaptive(Qd[q:q + 1], k, w["delta"], 0, storage=storage, trace=True, qid_base=qid_base + q,
+                            **opts_of(b_s))
+            rows_t.append({key: v[0].cpu().numpy() for key, v in r.items()})
+        traces[storage] = {"opts": opts_of(b_s), "rows": rows_t, "copy_error": ds.error(storage)}
+    traced = {"queries": trace_q, "storages": traces, "idx": ri[trace_q].cpu().numpy(),
+              "dist": rd[trace_q].cpu().numpy()}
+
     # ---- end to end through the public API with host buffers
     Qh = torch.from_numpy(Q).pin_memory()
     ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
@@ -490,28 +568,40 @@ def run_ours(args, rank, world, local_rank):
         "shared_coordinates": shared,
         "block_samples": blocks,
         "without_replacement": without_replacement,
+        "serving": serving,
         "exact_baseline": {"queries_per_s": round(world * nq / (exact_ms / 1e3), 3), "ms_per_batch": round(exact_ms, 4),
-                           "method": "tcgen05 BF16x3 screen GEMM + select + FP64 rerank (exact)",
+                           "method": f"tcgen05 {exact_screen.upper()} screen GEMM with the selection fused into its "
+                                     "epilogue (two passes, candidate lists) + FP32 ranking, FP64 for near ties "
+                                     "(exact)",
+                           "screen": exact_screen, "screens": exact_screens,
                            "agrees_with_simt_path": exact_agree,
                            "simt_f32_screen": {"queries_per_s": round(world * nq / (exact_simt_ms / 1e3), 3),
                                                "ms_per_batch": round(exact_simt_ms, 4)}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 5), "traffic": traffic,
-                     "dram_gbs": round(traffic / (kern_ms / 1e3) / 1e9, 2) if traffic else None,
-                     "dram_frac": round(traffic / (kern_ms / 1e3) / 1e9 / hbm, 5) if traffic else None,
-                     "kernel": f"knn_adaptive_ds call = round0_kernel<ElemF32> + adaptive_rounds_kernel<{best['threads']}, "
-                               "ElemF32>",
-                     "kernel_ms": round(kern_ms, 4),
+                     "traffic_source": "recorded ncu capture of this kernel source and launch configuration "
+                                       "(dram__bytes_read.sum + dram__bytes_write.sum of the round-loop kernel, "
+                                       "one call); null when either changed" if traffic else None,
+                     "dram_gbs": round(traffic / (loop_kern_ms / 1e3) / 1e9, 2) if traffic else None,
+                     "dram_frac": round(traffic / (loop_kern_ms / 1e3) / 1e9 / hbm, 5) if traffic else None,
+                     "kernel": f"adaptive_rounds_kernel<{best['threads']}, ElemF32>",
+                     "kernel_ms": round(loop_kern_ms, 4),
                      "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
+                     "call": {"kernels": "round0_kernel<ElemF32> + adaptive_rounds_kernel", "ms": round(kern_ms, 4),
+                              "round0_ms": round(r0_kern_ms, 4), "alg_bytes": alg_bytes_call,
+                              "frac": round(alg_bytes_call / (kern_ms / 1e3) / 1e9 / hbm, 5),
+                              "alg_bytes_builder": alg_bytes_builder},
                      "sector_gbs": round(sector_gbs, 2),
-                     "note": "algorithmic bytes: X once + round-0 sums written and read + 4 B per coordinate "
-                             "evaluation after round 0 + query rows; sector_gbs counts 32 B per evaluation (the DRAM "
-                             "granule a random 4-byte gather moves); dram_gbs = the captured DRAM traffic of one "
-                             "call over the live call time (round-0 pass + round loop)"},
+                     "note": "algorithmic bytes = 4 B (FP32 element) per coordinate evaluation: the round loop "
+                             "reads those of the rounds after round 0 plus the round-0 sums (4 B per pair); "
+                             "achieved = those bytes / the round-loop kernel's time from the library's CUDA events "
+                             "on the launching stream (mean of 3 calls); call = both kernels, 4 B per evaluation; "
+                             "sector_gbs counts 32 B per evaluation (the DRAM granule a random 4-byte gather moves)"},
         "e2e": {"value": round(world * nq / (e2e_ms / 1e3), 3), "unit": "queries/s",
                 "h2d_bytes_per_step": nq * m * 4, "d2h_bytes_per_step": nq * k * 16},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
+        "_traces": traced,
     }
     return result
 
@@ -554,7 +644,65 @@ def oracle_single_thread(X, Q, p, budget_s=3.0):
             "sample": f"{done} queries (first ones), {dt:.1f} s"}
 
 
-def cpu_baseline(args, budget_s=15.0, X=None, Q=None, cfg=None):
+def oracle_evidence(X, Q, traced, k, delta):
+    """The oracle's side of the CPU-baseline leg beyond its timing: replays
+    the traced GPU runs of a few queries of the timed batch in FP64 and
+    reports, per storage, the relative error of the GPU's FP32 sums against
+    the oracle's sums over the same samples (the same copy), the decisions
+    near their threshold (flagged, adopted from the GPU) and any other
+    mismatch; for the BF16 and FP8 copies also the per-sample error of the
+    copy's estimates against the FP32 data's at the same draws, beside its
+    bound e (2 sqrt(d^) + e); and the returned distances and recall against
+    the oracle's brute force."""
+    import oracle
+    qs = traced["queries"]
+    out = {"sample": f"{len(qs)} queries of the timed batch ({', '.join(map(str, qs))}), run alone with their "
+                     "decision log (same Philox query ids) and replayed round by round by the oracle (FP64)"}
+    for storage, tr in traced["storages"].items():
+        o = tr["opts"]
+        kw = dict(delta=delta, seed=0, tol=1e-5, bound=o["bound"], c_alpha=o["c_alpha"], B0=o["B0"], B=o["B"],
+                  grow=o["grow"])
+        rels, near, bad, pairs = [], 0, 0, 0
+        per_sample, ratio = [], []
+        for q, g in zip(qs, tr["rows"]):
+            r = oracle.adaptive(X, Q[q:q + 1], oracle.make_params(k, qid=q, storage=storage, **kw),
+                                replay=g["code"][None, :])
+            st = r["stats"][0]
+            near += st["near"]
+            bad += st["mismatch"] + st["log_inconsistent"]
+            So, Sg, T = r["S"][0], g["S"].astype(np.float64), r["T"][0]
+            ev = T > 0
+            pairs += int(ev.sum())
+            rels.append(np.abs(Sg[ev] - So[ev]) / np.maximum(np.abs(So[ev]), 1e-300))
+            if storage != "f32":   # the same draws over the FP32 data
+                rd_ = oracle.adaptive(X, Q[q:q + 1], oracle.make_params(k, qid=q, storage="f32", **kw),
+                                      replay=g["code"][None, :])
+                Sd, Td = rd_["S"][0], rd_["T"][0]
+                sel = (Td > 0) & (Td == T)
+                e = tr["copy_error"]
+                err = np.abs(Sg[sel] - Sd[sel]) / Td[sel]
+                bound = e * (2.0 * np.sqrt(np.maximum(Sg[sel], 0.0) / Td[sel]) + e)
+                per_sample.append(err)
+                ratio.append(np.where(bound > 0, err / np.maximum(bound, 1e-300), 0.0))
+        rel = np.concatenate(rels)
+        rec = {"pairs": pairs, "estimate_rel_err_max": float(rel.max()),
+               "estimate_rel_err_p99": float(np.percentile(rel, 99)), "near_threshold_flagged": int(near),
+               "decisions_mismatched": int(bad)}
+        if per_sample:
+            ps, ra = np.concatenate(per_sample), np.concatenate(ratio)
+            rec.update({"copy_error_e": tr["copy_error"], "copy_vs_data_per_sample_err_max": float(ps.max()),
+                        "copy_vs_data_per_sample_err_p99": float(np.percentile(ps, 99)),
+                        "bound_ratio_max": float(ra.max())})
+        out[storage] = rec
+    ti, td = oracle.exact_knn(X, Q[qs], k)
+    gd = traced["dist"]
+    out["returned_distances"] = {"rel_err_max": float(np.max(np.abs(gd - td) / np.maximum(np.abs(td), 1e-300))),
+                                 "vs": "oracle FP64 brute force"}
+    out["recall_vs_oracle"] = recall_of(traced["idx"], gd, ti, td)
+    return out
+
+
+def cpu_baseline(args, budget_s=15.0, X=None, Q=None, cfg=None, traced=None):
     import oracle
     w = WORKLOAD
     if X is None:
@@ -571,7 +719,8 @@ def cpu_baseline(args, budget_s=15.0, X=None, Q=None, cfg=None):
     return {"value": round(done / dt, 4), "unit": "queries/s", "cores": threads, "kind": "oracle",
             "sample": f"{done} of {Q.shape[0]} queries (first ones), C_alpha={sch['c_alpha']}, "
                       f"B0={sch['B0']} B={sch['B']} grow={sch['grow']}, FP64, OpenMP over queries, {dt:.1f} s",
-            "cpu_model": cpu_model(), "single_thread": oracle_single_thread(X, Q, p)}
+            "cpu_model": cpu_model(), "single_thread": oracle_single_thread(X, Q, p),
+            **({"evidence": oracle_evidence(X, Q, traced, w["k"], w["delta"])} if traced else {})}
 
 
 def run_reference(args, rank, world):
@@ -928,6 +1077,8 @@ def main():
     ap.add_argument("--sweep-gaps", dest="sweep_gaps", default=None, help="comma-separated gap ratios")
     ap.add_argument("--sweep-variants", dest="sweep_variants", default=None, help="comma-separated variant names")
     ap.add_argument("--serve-seconds", dest="serve_seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds-bench", dest="serve_seconds_bench", type=float, default=2.0,
+                    help="arrival window of each serving phase of the default line")
     ap.add_argument("--serve-scale", dest="serve_scale", type=float, default=1.0)
     ap.add_argument("--serve-slots", dest="serve_slots", type=int, default=4)
     ap.add_argument("--serve-mem", dest="serve_mem", type=int, default=24, help="GiB for in-flight round state")
@@ -974,9 +1125,12 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     res = run_ours(args, rank, world, local_rank)
+    traced = res.pop("_traces", None)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(args, cfg=res["config"])
+            cb = cpu_baseline(args, cfg=res["config"], traced=traced)
+            res["precision"] = cb.pop("evidence", None)
+            res["cpu_baseline"] = cb
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -355,6 +355,17 @@ knn_status knn_device_status(int32_t* out);
  * per query and atomics by one thread); any other returns KNN_EUNSUPPORTED. */
 knn_status knn_phase_clocks(uint64_t* out, int32_t reset);
 
+/* Kernel timing of knn_adaptive_ds(_multi) calls (measurement; no
+ * counterpart in the paper). knn_kernel_timing(1) makes later calls record
+ * CUDA events on their stream around the point-major round-0 pass and the
+ * round-loop kernel (do not enable it while capturing a CUDA graph);
+ * knn_kernel_timing(0) stops. knn_kernel_times waits for the last recorded
+ * event and writes out_ms[0] = total milliseconds of the round-0 passes and
+ * out_ms[1] = of the round-loop kernels, over every call since the last
+ * reset (2 host doubles); reset != 0 starts a new total. */
+knn_status knn_kernel_timing(int32_t enable);
+knn_status knn_kernel_times(double* out_ms, int32_t reset);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* knn_last_error(void);
 

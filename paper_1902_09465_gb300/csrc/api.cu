@@ -4,6 +4,8 @@
 
 #include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "knn_internal.h"
 
@@ -164,7 +166,60 @@ unsigned long long* phase_clocks_ptr() {
 unsigned long long* phase_clocks_ptr() { return nullptr; }
 #endif
 
+// Events of the marks of the last timed call(s), host side.
+static std::mutex g_timing_mu;
+static bool g_timing = false;
+static std::vector<std::pair<cudaEvent_t, int>> g_marks;  // (event, kind) in stream order
+static std::vector<cudaEvent_t> g_event_pool;
+
+bool kernel_timing_on() { return g_timing; }
+
+void kernel_mark(cudaStream_t stream, int kind) {
+  std::lock_guard<std::mutex> lock(g_timing_mu);
+  if (!g_timing) return;
+  cudaEvent_t ev;
+  if (g_event_pool.empty()) {
+    if (cudaEventCreate(&ev) != cudaSuccess) return;
+  } else {
+    ev = g_event_pool.back();
+    g_event_pool.pop_back();
+  }
+  if (cudaEventRecord(ev, stream) != cudaSuccess) {
+    g_event_pool.push_back(ev);
+    return;
+  }
+  g_marks.emplace_back(ev, kind);
+}
+
 }  // namespace knn
+
+extern "C" knn_status knn_kernel_timing(int32_t enable) {
+  knn::clear_error();
+  std::lock_guard<std::mutex> lock(knn::g_timing_mu);
+  knn::g_timing = enable != 0;
+  return KNN_OK;
+}
+
+extern "C" knn_status knn_kernel_times(double* out_ms, int32_t reset) {
+  knn::clear_error();
+  if (!out_ms) return knn::set_error("knn_kernel_times: null pointer"), KNN_EINVAL;
+  std::lock_guard<std::mutex> lock(knn::g_timing_mu);
+  out_ms[0] = out_ms[1] = 0.0;
+  auto& mk = knn::g_marks;
+  knn_status s = KNN_OK;
+  if (!mk.empty()) s = knn::cuda_check(cudaEventSynchronize(mk.back().first), "cudaEventSynchronize");
+  for (size_t i = 0; s == KNN_OK && i + 1 < mk.size(); ++i) {
+    if (mk[i].second > 1) continue;
+    float ms = 0.0f;
+    s = knn::cuda_check(cudaEventElapsedTime(&ms, mk[i].first, mk[i + 1].first), "cudaEventElapsedTime");
+    out_ms[mk[i].second] += ms;
+  }
+  if (reset) {
+    for (auto& e : mk) knn::g_event_pool.push_back(e.first);
+    mk.clear();
+  }
+  return s;
+}
 
 extern "C" knn_status knn_phase_clocks(uint64_t* out, int32_t reset) {
   knn::clear_error();

@@ -141,6 +141,7 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
     ac.qids = a.qids ? a.qids + q0 : nullptr;
     ac.qid_base = a.qid_base + (uint64_t)q0;
     s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
+    if (r0) kernel_mark(stream, 0);
     if (s == KNN_OK && r0) {
       if constexpr (E::kPerm) {
         const unsigned blocks = (unsigned)((n + kR0SharedThreads - 1) / kR0SharedThreads);
@@ -170,7 +171,9 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
         s = cuda_check(cudaGetLastError(), "round0_kernel launch");
       }
     }
+    kernel_mark(stream, 1);
     if (s == KNN_OK) s = launch_rounds<E>(p, ac, stream);
+    kernel_mark(stream, 2);
   }
   ws.release();
   return s;

@@ -71,6 +71,13 @@ knn_status device_status_ptr(int** out);
 // (16 counters) in a library built with KNN_PHASE_TIMING; null otherwise.
 unsigned long long* phase_clocks_ptr();
 
+// Kernel timing of the adaptive calls (knn_kernel_timing): when enabled,
+// kernel_mark(stream, kind) records a CUDA event on the stream; the time from
+// one mark to the next is charged to the earlier mark's kind (0: round-0 pass,
+// 1: round loop, 2: end of a call).
+bool kernel_timing_on();
+void kernel_mark(cudaStream_t stream, int kind);
+
 }  // namespace knn
 
 // A resident dataset (see knn_dataset_create).

@@ -12,7 +12,7 @@
 
 namespace knn {
 
-constexpr int kRerankNT = 256;
+constexpr int kRerankNT = 512;
 constexpr int kRerankCap = 4096;  // candidates sorted at once
 
 // Keys are (bits of a non-negative double, index); +inf bits mark no point.
@@ -122,7 +122,8 @@ template <int NT>
 __global__ void __launch_bounds__(NT) refine_kernel(const float* __restrict__ X, int64_t n, int m,
                                                     const float* __restrict__ Q, const int64_t* __restrict__ cand,
                                                     int ncand, const int32_t* __restrict__ cnt, int k,
-                                                    int64_t* out_idx, double* out_dist, int l1, int vec, int cap) {
+                                                    int64_t* out_idx, double* out_dist, int l1, int vec, int cap,
+                                                    const float* __restrict__ cand_d, const float* __restrict__ eq) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
   int64_t* idx = reinterpret_cast<int64_t*>(key + cap);
@@ -140,17 +141,66 @@ __global__ void __launch_bounds__(NT) refine_kernel(const float* __restrict__ X,
   const bool full = c > ncand || (ncand > 0 && c > 0 && cr[0] == -2);
   __syncthreads();
   if (!full) {
-    // 1. FP32 distances, keyed (d32 bits, slot)
-    const int P = next_pow2(c < 2 ? 2 : c);
-    for (int t = threadIdx.x; t < P; t += NT) k32[t] = ~0ull;
-    __syncthreads();
-    for (int t = warp; t < c; t += NT / 32) {
-      const int64_t id = cr[t];
-      if (id < 0 || id >= n) continue;
-      const float d = row_dist32(X + (size_t)id * m, qs, m, lane, l1 != 0, vec != 0);
-      if (lane == 0 && !isnan(d)) k32[t] = ((uint64_t)f2key(d) << 32) | (uint32_t)t;
+    int P = next_pow2(c < 2 ? 2 : c);
+    if (cand_d) {
+      // 0. a screen's candidates with their screened values D~ (|D~ - d| <=
+      // E_q): FP32 distances of the k smallest by D~ bound the k-th distance,
+      // d_(k) <= D*/(1 - rel) with D* their largest d32, and every true
+      // k-nearest point j has D~_j <= d_j + E_q <= D*/(1 - rel) + E_q; only
+      // the candidates below that need their FP32 distance.
+      float* d32s = reinterpret_cast<float*>(key);  // scratch until step 3
+      for (int t = threadIdx.x; t < P; t += NT)
+        k32[t] = t < c ? ((uint64_t)f2key(cand_d[(size_t)q * ncand + t]) << 32) | (uint32_t)t : ~0ull;
+      __syncthreads();
+      bitonic_sort_u64<NT>(k32, P);
+      const int kk = min(k, c);
+      float dmax = 0.0f;
+      for (int t = warp; t < kk; t += NT / 32) {
+        const int64_t id = cr[(uint32_t)k32[t]];
+        const float d = row_dist32(X + (size_t)id * m, qs, m, lane, l1 != 0, vec != 0);
+        if (lane == 0) d32s[t] = d;
+        dmax = fmaxf(dmax, d);
+      }
+      if (lane != 0) dmax = 0.0f;
+      __shared__ float s_dmax;
+      if (threadIdx.x == 0) s_dmax = 0.0f;
+      __syncthreads();
+      if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(&s_dmax), __float_as_uint(dmax));
+      __syncthreads();
+      const float cut2 = (s_dmax / (1.0f - rel) * (1.0f + 4.0f * u) + eq[q]) * (1.0f + 4.0f * u);
+      int w2 = 0;
+      for (int b = 0; b < c; b += NT)
+        w2 += __syncthreads_count(b + threadIdx.x < c && key2f((uint32_t)(k32[b + threadIdx.x] >> 32)) <= cut2);
+      w2 = max(w2, kk);
+      for (int t = kk + warp; t < w2; t += NT / 32) {
+        const int64_t id = cr[(uint32_t)k32[t]];
+        const float d = row_dist32(X + (size_t)id * m, qs, m, lane, l1 != 0, vec != 0);
+        if (lane == 0) d32s[t] = d;
+      }
+      __syncthreads();
+      // 1. keyed (d32 bits, slot) for the step below
+      uint64_t nk[8];
+      const int P2 = next_pow2(w2 < 2 ? 2 : w2);
+      int e = 0;
+      for (int t = threadIdx.x; t < P2; t += NT, ++e)
+        nk[e] = t < w2 && !isnan(d32s[t]) ? ((uint64_t)f2key(d32s[t]) << 32) | (uint32_t)k32[t] : ~0ull;
+      __syncthreads();
+      e = 0;
+      for (int t = threadIdx.x; t < P2; t += NT, ++e) k32[t] = nk[e];
+      __syncthreads();
+      P = P2;
+    } else {
+      // 1. FP32 distances, keyed (d32 bits, slot)
+      for (int t = threadIdx.x; t < P; t += NT) k32[t] = ~0ull;
+      __syncthreads();
+      for (int t = warp; t < c; t += NT / 32) {
+        const int64_t id = cr[t];
+        if (id < 0 || id >= n) continue;
+        const float d = row_dist32(X + (size_t)id * m, qs, m, lane, l1 != 0, vec != 0);
+        if (lane == 0 && !isnan(d)) k32[t] = ((uint64_t)f2key(d) << 32) | (uint32_t)t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     bitonic_sort_u64<NT>(k32, P);
     // 2. the window: a prefix of the sorted keys
     int v = 0;
@@ -234,7 +284,7 @@ __global__ void __launch_bounds__(NT) refine_kernel(const float* __restrict__ X,
 
 knn_status launch_refine(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, const int32_t* cnt, int32_t k, int64_t* out_idx, double* out_dist,
-                         cudaStream_t stream, int32_t metric) {
+                         cudaStream_t stream, int32_t metric, const float* cand_d, const float* eq) {
   // sort capacity: every candidate, and room for a chunk of points beside the
   // running top-k when a list asks for every point
   int cap = 2;
@@ -246,14 +296,15 @@ knn_status launch_refine(const float* X, int64_t n, int32_t m, const float* Q, i
   if (s != KNN_OK) return s;
   const int vec = (m % 4 == 0) && (((uintptr_t)X & 15) == 0);
   refine_kernel<kRerankNT><<<nq, kRerankNT, smem, stream>>>(X, n, m, Q, cand, ncand, cnt, k, out_idx, out_dist,
-                                                            metric == KNN_METRIC_L1 ? 1 : 0, vec, cap);
+                                                            metric == KNN_METRIC_L1 ? 1 : 0, vec, cap, cand_d,
+                                                            eq);
   return cuda_check(cudaGetLastError(), "refine_kernel launch");
 }
 
 knn_status launch_rerank(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, int32_t k, int64_t* out_idx, double* out_dist, cudaStream_t stream,
                          int32_t metric) {
-  return launch_refine(X, n, m, Q, nq, cand, ncand, nullptr, k, out_idx, out_dist, stream, metric);
+  return launch_refine(X, n, m, Q, nq, cand, ncand, nullptr, k, out_idx, out_dist, stream, metric, nullptr, nullptr);
 }
 
 }  // namespace knn

@@ -28,14 +28,15 @@
 // D~_j <= d_j + E_q <= cut_q.
 //
 // Kernel layout: one CTA per SM, persistent over tiles of 128 points x 256
-// queries, 6 warps. Warp 0 lane 0 issues TMA loads (128-byte swizzle, 64
+// queries, 10 warps. Warp 0 lane 0 issues TMA loads (128-byte swizzle, 64
 // K-elements per stage, 4 stages); warp 1 lane 0 issues tcgen05.mma (M = 128,
 // N = 256, K = 16, FP32 accumulator in TMEM) into one of two accumulators of
 // 256 columns, so the epilogue of one tile overlaps the MMAs of the next;
-// warps 2-5 read the accumulator (tcgen05.ld 32x32b, one TMEM lane quarter
-// each) and run the pass's epilogue. Every mbarrier wait is bounded: a wait
-// that gives up records a code in the library status word, the CTA waits for
-// its TMA copies and MMAs in flight and frees its tensor memory before it exits.
+// warps 2-9 read the accumulator (tcgen05.ld 32x32b; two warps per TMEM lane
+// quarter, 128 columns each) and run the pass's epilogue. Every mbarrier wait
+// is bounded: a wait that gives up records a code in the library status
+// word, the CTA waits for its TMA copies and MMAs in flight and frees its
+// tensor memory before it exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -54,9 +55,10 @@ namespace knn {
 
 knn_status launch_refine(const float* X, int64_t n, int32_t m, const float* Q, int32_t nq, const int64_t* cand,
                          int32_t ncand, const int32_t* cnt, int32_t k, int64_t* out_idx, double* out_dist,
-                         cudaStream_t stream, int32_t metric);
+                         cudaStream_t stream, int32_t metric, const float* cand_d = nullptr,
+                         const float* eq = nullptr);
 
-constexpr int kTcM = 128, kTcN = 256, kTcK = 64, kTcStages = 4, kTcThreads = 192;
+constexpr int kTcM = 128, kTcN = 256, kTcK = 64, kTcStages = 4, kTcThreads = 320;
 constexpr int kTcABytes = kTcM * kTcK * 2;  // 16 KB
 constexpr int kTcBBytes = kTcN * kTcK * 2;  // 32 KB
 constexpr int kTcCols = 2 * kTcN;           // two accumulators of 256 FP32 columns
@@ -140,31 +142,36 @@ __device__ __forceinline__ void umma_f16kind(uint32_t d_tmem, uint64_t adesc, ui
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-__device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+// Barrier of the 256 epilogue threads (named barrier 1).
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// OR of a predicate over the 128 epilogue threads (named barrier 1).
+// OR of a predicate over the 256 epilogue threads (named barrier 1).
 __device__ __forceinline__ bool epi_any(bool p) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "bar.red.or.pred q, 1, 256, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
       : "r"((uint32_t)p)
       : "memory");
   return r != 0;
+}
+
+__device__ __forceinline__ void tmem_ld_x32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Minimum over the 32 lanes of each of 16 values: halve the set per step
@@ -215,6 +222,7 @@ struct ScreenArgs {
   const float* cut;   // pass 2: [nq] cut_q
   int* cnt;           // pass 2: [nq] candidates appended (may exceed cap)
   int64_t* cand;      // pass 2: [nq][cap] candidate points
+  float* cand_d;      // pass 2: [nq][cap] their screened values D~
   int cap;
   int* status;        // library status word
 };
@@ -232,6 +240,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* scnt = reinterpret_cast<int*>(tmem_slot + 4);                 // [256] staged pairs per column (pass 2)
   uint8_t* srow = reinterpret_cast<uint8_t*>(scnt + kTcN);           // [256][kStage] their rows in the tile
+  float2* colv = reinterpret_cast<float2*>(srow + kTcN * kStage);    // [256] per-column constants of the tile
+  float* sval = reinterpret_cast<float*>(colv + kTcN);                // [256][kStage] their screened values
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages);
   const uint32_t accf0 = smem_u32(bars + 2 * kTcStages), acce0 = smem_u32(bars + 2 * kTcStages + 2);
@@ -244,7 +254,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 128);  // every epilogue thread arrives once per tile
+      mbar_init(acce0 + 8 * b, 256);  // every epilogue thread arrives once per tile
     }
     mbar_init(drain, 1);
     *err = 0;
@@ -318,16 +328,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_wait(drain, 0, kSpinDefault);
     }
     __syncwarp();
-  } else {  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+  } else {  // epilogue: warps 2-9; warp w reads TMEM lanes 32 (w % 4) .. + 31, columns 128 ((w - 2) / 4) .. + 127
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int row = quarter * 32 + lane;
+    const int et = threadIdx.x - 64;  // 0..255: the column this thread stages and flushes
     const float c2 = *a.c2;
     uint32_t tc = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++tc) {
       const int buf = tc & 1;
       const bool ok = !*err && mbar_wait(accf0 + 8 * buf, (tc >> 1) & 1u, a.limit);
-      // the four epilogue warps take the same decision, so that none of them
-      // waits at a named barrier that another has left
+      // the epilogue warps take the same decision, so that none of them waits
+      // at a named barrier that another has left
       if (epi_any(!ok)) {
         *err = 1;
         break;
@@ -338,34 +350,58 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int q0 = (t % a.nqt) * kTcN;
       const int64_t p = p0 + row;
       const float xv = p < a.n ? __ldg(a.xn + p) : INFINITY;
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTcN);
-      for (int c0 = 0; c0 < kTcN; c0 += 16) {
-        float v[16];
-        tmem_ld_x16(taddr + (uint32_t)c0, v);
+      {  // the tile's per-column constants: ||qc||^2 and the cut (-inf: no query)
+        const int q = q0 + et;
+        colv[et] = q < a.nq ? make_float2(__ldg(a.qn + q), a.pass == 2 ? __ldg(a.cut + q) : 0.0f)
+                            : make_float2(0.0f, -INFINITY);
+      }
+      epi_sync();
+      const uint32_t taddr =
+          tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTcN) + (uint32_t)(half * (kTcN / 2));
+      for (int c0 = 0; c0 < kTcN / 2; c0 += 32) {
+        float v[32];
+        tmem_ld_x32(taddr + (uint32_t)c0, v);
+        const int cb = half * (kTcN / 2) + c0;  // tile column of v[0]
         if (a.pass == 1) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int q = q0 + c0 + j;
-            v[j] = (p < a.n && q < a.nq) ? fmaf(c2, v[j], xv + __ldg(a.qn + q)) : INFINITY;
+          for (int j = 0; j < 32; ++j) {
+            const float2 cv = colv[cb + j];
+            v[j] = cv.y == -INFINITY ? INFINITY : fmaf(c2, v[j], xv + cv.x);
           }
-          const float mn = warp_min16(v, lane);
-          const int q = q0 + c0 + (lane >> 1);
-          if ((lane & 1) == 0 && q < a.nq) a.gmin[(size_t)q * a.nunits + pt_vis * 4 + quarter] = mn;
-        } else if (p < a.n) {
-          // stage passing pairs per query column in shared memory (a global
-          // atomic per pair here would stall the warp for its round trip)
+          const float mn0 = warp_min16(*reinterpret_cast<float(*)[16]>(v), lane);
+          const float mn1 = warp_min16(*reinterpret_cast<float(*)[16]>(v + 16), lane);
+          if ((lane & 1) == 0) {
+            const size_t unit = (size_t)pt_vis * 4 + quarter;
+            const int qa = q0 + cb + (lane >> 1), qb = qa + 16;
+            if (qa < a.nq) a.gmin[(size_t)qa * a.nunits + unit] = mn0;
+            if (qb < a.nq) a.gmin[(size_t)qb * a.nunits + unit] = mn1;
+          }
+        } else {
+          uint32_t hit = 0;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int c = c0 + j, q = q0 + c;
-            if (q < a.nq) {
-              const float D = fmaf(c2, v[j], xv + __ldg(a.qn + q));
-              if (D <= __ldg(a.cut + q)) {
-                const int slot = atomicAdd(&scnt[c], 1);
-                if (slot < kStage) {
-                  srow[c * kStage + slot] = (uint8_t)row;
-                } else {  // a crowded column: straight to the global list
-                  const int pos = atomicAdd(a.cnt + q, 1);
-                  if (pos < a.cap) a.cand[(size_t)q * a.cap + pos] = p;
+          for (int j = 0; j < 32; ++j) {
+            const float2 cv = colv[cb + j];
+            v[j] = fmaf(c2, v[j], xv + cv.x);
+            hit |= (v[j] <= cv.y ? 1u : 0u) << j;
+          }
+          if (p >= a.n) hit = 0;
+          if (__any_sync(0xffffffffu, hit != 0)) {
+            // stage passing pairs per column in shared memory (a global atomic
+            // per pair here would stall the warp for its round trip)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (!((hit >> j) & 1u)) continue;
+              const int c = cb + j;
+              const int slot = atomicAdd(&scnt[c], 1);
+              if (slot < kStage) {
+                srow[c * kStage + slot] = (uint8_t)row;
+                sval[c * kStage + slot] = v[j];
+              } else {  // a crowded column: straight to the global list
+                const int q = q0 + c;
+                const int pos = atomicAdd(a.cnt + q, 1);
+                if (pos < a.cap) {
+                  a.cand[(size_t)q * a.cap + pos] = p;
+                  a.cand_d[(size_t)q * a.cap + pos] = v[j];
                 }
               }
             }
@@ -376,18 +412,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_arrive(acce0 + 8 * buf);  // the accumulator is free for the next tile's MMAs
       if (a.pass == 2) {
         // flush: one global reservation per column with staged pairs
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        for (int c = threadIdx.x - 64; c < kTcN; c += 128) {
-          const int cnt_c = min(scnt[c], kStage);
-          if (cnt_c > 0) {
-            const int q = q0 + c;
-            const int base = atomicAdd(a.cnt + q, cnt_c);
-            for (int i = 0; i < cnt_c; ++i)
-              if (base + i < a.cap) a.cand[(size_t)q * a.cap + base + i] = p0 + srow[c * kStage + i];
-          }
-          scnt[c] = 0;
+        epi_sync();
+        const int cnt_c = min(scnt[et], kStage);
+        if (cnt_c > 0) {
+          const int q = q0 + et;
+          const int base = atomicAdd(a.cnt + q, cnt_c);
+          for (int i = 0; i < cnt_c; ++i)
+            if (base + i < a.cap) {
+              a.cand[(size_t)q * a.cap + base + i] = p0 + srow[et * kStage + i];
+              a.cand_d[(size_t)q * a.cap + base + i] = sval[et * kStage + i];
+            }
         }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
+        scnt[et] = 0;  // (the next tile stages after its own barrier)
       }
     }
   }
@@ -411,14 +447,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // cut_q = tau_q + 2 E_q (plus a few units of roundoff), tau_q the k-th
 // smallest group minimum of pass 1; +inf when there are fewer than k groups.
-// Also zeroes the query's candidate count for pass 2.
+// Also stores E_q (for the ranking) and zeroes the query's candidate count
+// for pass 2.
 constexpr int kCutNT = 256;
 
 __global__ void __launch_bounds__(kCutNT) screen_cut_kernel(const float* __restrict__ gmin, int nunits, int k, int m,
                                                             const float* __restrict__ qn,
                                                             const unsigned* __restrict__ xn_max_bits,
                                                             float c_cross, float c_square, float* __restrict__ cut,
-                                                            int* __restrict__ cnt) {
+                                                            float* __restrict__ eq, int* __restrict__ cnt) {
   __shared__ uint32_t hist[kHistBins];
   __shared__ uint32_t buf[kSelCap];
   __shared__ BlockScratch<kCutNT> bs;
@@ -435,19 +472,20 @@ __global__ void __launch_bounds__(kCutNT) screen_cut_kernel(const float* __restr
     tau = key2f(buf[k - 1]);
   }
   if (threadIdx.x == 0) {
+    // FP32 arithmetic on non-negative terms: a few units of roundoff,
+    // covered by the factor 1.001 (the coefficients carry their own margins)
+    const float u = 1.0f / 16777216.0f;
+    const float gm = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);  // the norms' FP32 sums
+    const float xmax = sqrtf(__uint_as_float(*xn_max_bits) * (1.0f + gm));
+    const float qq = sqrtf(qn[q] * (1.0f + gm));
+    const float E = 1.001f * (c_cross * xmax * qq + c_square * (xmax + qq) * (xmax + qq));
     float c = INFINITY;
     if (isfinite(tau)) {
-      // FP32 arithmetic on non-negative terms: a few units of roundoff,
-      // covered by the factor 1.001 (the coefficients carry their own margins)
-      const float u = 1.0f / 16777216.0f;
-      const float gm = (float)(m + 2) * u / (1.0f - (float)(m + 2) * u);  // the norms' FP32 sums
-      const float xmax = sqrtf(__uint_as_float(*xn_max_bits) * (1.0f + gm));
-      const float qq = sqrtf(qn[q] * (1.0f + gm));
-      const float E = 1.001f * (c_cross * xmax * qq + c_square * (xmax + qq) * (xmax + qq));
       const float x = tau + 2.0f * E;
       c = x + 8.0f * u * fabsf(x) + 1e-30f;
     }
     cut[q] = c;
+    eq[q] = E * (1.0f + 8.0f * u);
     cnt[q] = 0;
   }
 }
@@ -590,7 +628,7 @@ static knn_status make_map(CUtensorMap* map, const void* base, int64_t rows, int
 
 static size_t screen_smem_bytes() {
   return 1024 + (size_t)kTcStages * (kTcABytes + kTcBBytes) + (2 * kTcStages + 5) * 8 + 16 + kTcN * 4 +
-         kTcN * kStage;
+         kTcN * kStage + kTcN * 8 + kTcN * kStage * 4;
 }
 
 static int kind_of_screen(int32_t screen) {
@@ -651,8 +689,10 @@ struct TcCarve {
   float* c2;
   float* gmin;
   float* cut;
+  float* eq;
   int* cnt;
   int64_t* cand;
+  float* cand_d;
 };
 
 static size_t carve_tc(Carve& cv, int64_t n, int32_t nq, int Kt, TcCarve* out) {
@@ -665,8 +705,10 @@ static size_t carve_tc(Carve& cv, int64_t n, int32_t nq, int Kt, TcCarve* out) {
   c.c2 = cv.take<float>(1);
   c.gmin = cv.take<float>((size_t)nq * 4 * npt);
   c.cut = cv.take<float>((size_t)nq);
+  c.eq = cv.take<float>((size_t)nq);
   c.cnt = cv.take<int>((size_t)nq);
   c.cand = cv.take<int64_t>((size_t)nq * kScreenCap);
+  c.cand_d = cv.take<float>((size_t)nq * kScreenCap);
   if (out) *out = c;
   return cv.off;
 }
@@ -681,7 +723,7 @@ size_t exact_tc_workspace(int64_t n, int32_t m, int32_t nq, int32_t screen) {
 // the visited groups' minima then lies near the (s k)-th smallest screened
 // value, so about s k points (plus the screen's margin) become candidates.
 static int pass1_stride(int64_t npt, int k) {
-  int s = std::max(1, std::min(16, 64 / k));
+  int s = std::max(1, std::min(16, 128 / k));
   while (s > 1 && 4 * ((npt + s - 1) / s) < 4 * (int64_t)k) --s;
   return s;
 }
@@ -750,6 +792,7 @@ knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32
   a.cut = c.cut;
   a.cnt = c.cnt;
   a.cand = c.cand;
+  a.cand_d = c.cand_d;
   a.cap = kScreenCap;
   a.status = status;
 
@@ -786,7 +829,7 @@ knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32
     const double c_cross = 1.5 * 2.0 * (gacc + prod) * 1.01;
     const double c_square = 1.5 * (gm + 6.0 * u);
     screen_cut_kernel<<<nq, kCutNT, 0, stream>>>(c.gmin, a.nunits, k, m, c.qn, ds->xcn_max, (float)c_cross,
-                                                 (float)c_square, c.cut, c.cnt);
+                                                 (float)c_square, c.cut, c.eq, c.cnt);
     s = cuda_check(cudaGetLastError(), "screen_cut_kernel launch");
   }
   if (s == KNN_OK) {  // pass 2: candidates
@@ -797,7 +840,8 @@ knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32
     s = cuda_check(cudaGetLastError(), "screen_tc_kernel launch (pass 2)");
   }
   if (s == KNN_OK)
-    s = launch_refine(ds->X, n, m, Q, nq, c.cand, kScreenCap, c.cnt, k, out_idx, out_dist, stream, KNN_METRIC_L2SQ);
+    s = launch_refine(ds->X, n, m, Q, nq, c.cand, kScreenCap, c.cnt, k, out_idx, out_dist, stream, KNN_METRIC_L2SQ,
+                      c.cand_d, c.eq);
   ws.release();
   return s;
 }

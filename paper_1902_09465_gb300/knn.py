@@ -62,6 +62,8 @@ _SIGS = {
     "knn_exact_ds": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_int32, _P, _P, _P, C.c_size_t, _P]),
     "knn_device_status": (C.c_int, [C.POINTER(C.c_int32)]),
     "knn_debug_wait_limit": (C.c_int, [C.c_int64]),
+    "knn_kernel_timing": (C.c_int, [C.c_int32]),
+    "knn_kernel_times": (C.c_int, [C.POINTER(C.c_double), C.c_int32]),
     "knn_phase_clocks": (C.c_int, [C.POINTER(C.c_uint64), C.c_int32]),
     "knn_adaptive_ds_multi_workspace_size": (C.c_size_t, [_P, C.c_int32, C.c_int32, C.POINTER(Opts)]),
     "knn_adaptive_ds_multi": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_double, C.c_uint64,
@@ -349,6 +351,20 @@ def debug_wait_limit(tries: int) -> None:
     """Test hook: the tensor-core kernels' pipeline waits give up after
     `tries` polls (negative: the default) -- knn_debug_wait_limit."""
     _check(lib().knn_debug_wait_limit(int(tries)))
+
+
+def kernel_timing(enable: bool) -> None:
+    """knn_kernel_timing: record CUDA events around the round-0 pass and the
+    round-loop kernel of later adaptive dataset calls (not while capturing)."""
+    _check(lib().knn_kernel_timing(1 if enable else 0))
+
+
+def kernel_times(reset: bool = True):
+    """knn_kernel_times: (round-0 pass ms, round-loop ms) summed over the
+    calls since the last reset."""
+    out = (C.c_double * 2)()
+    _check(lib().knn_kernel_times(out, 1 if reset else 0))
+    return float(out[0]), float(out[1])
 
 
 def device_status() -> int:
