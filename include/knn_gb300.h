@@ -64,9 +64,9 @@ typedef enum { KNN_METRIC_L2SQ = 0, KNN_METRIC_L1 = 1 } knn_metric;
  * the default), or without replacement (the footnote to Section 4: a cipher on
  * [m]): the pair's s-th draw is pi(s), pi a permutation of [0, m) keyed per
  * (seed, point, query) -- an 8-round balanced Feistel network on 2h bits
- * (4^h >= m, h >= 1) whose round keys are the eight 32-bit words of
- * Philox4x64-10 at counter (2^64 - 1, point & mask_p, query & mask_q, 0), key
- * (seed, 0), round function fmix32(R xor k_r) mod 2^h (MurmurHash3's
+ * (4^h >= m, h >= 1) whose round keys are the words of blocks 2^32 - 2 and
+ * 2^32 - 1 of the pair's Philox4x32-10 stream (counter and key as for the
+ * draws with replacement), round function fmix32(R xor k_r) mod 2^h (MurmurHash3's
  * finaliser), cycle-walked onto [0, m). The bounds are unchanged (Hoeffding's
  * inequality holds for sampling without replacement). */
 typedef enum { KNN_SAMPLE_WITH = 0, KNN_SAMPLE_WITHOUT = 1 } knn_sampling;
@@ -113,9 +113,10 @@ size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, 
  *
  * For every query q (row q of Q, nq x m) independently:
  *   round r draws B_r new coordinates j ~ U[0, m) for every still-active
- *   point i (Philox4x64-10, key (seed, 0), counter (s/8, i & mask_p,
- *   (qid_base+q) & mask_q, 0), 32-bit word s mod 8 scaled by floor(w m / 2^32),
- *   s = 0,1,2,... the point's sample number); sums (X[i,j] - Q[q,j])^2 into a
+ *   point i (Philox4x32-10, key (low and high words of seed), counter
+ *   (s/4, i & mask_p, low and high words of (qid_base+q) & mask_q), word
+ *   s mod 4 scaled by floor(w m / 2^32), s = 0,1,2,... the point's sample
+ *   number); sums (X[i,j] - Q[q,j])^2 into a
  *   running FP32 sum S_i (Kahan-compensated), or computes the exact distance
  *   once T + B_r >= m (Algorithm 1's exact-evaluation step at T = m);
  *   with span = max(X, Q[q]) - min(X, Q[q]) (the normalisation of Section 3)

@@ -63,7 +63,7 @@ def lib():
         if _lib is None:
             L = C.CDLL(build())
             P = C.c_void_p
-            L.orc_philox4x64_10.argtypes = [P, P, P]
+            L.orc_philox4x32_10.argtypes = [P, P, P]
             L.orc_coordinate.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int32,
                                          C.c_uint64, C.c_uint64]
             L.orc_coordinate.restype = C.c_int32
@@ -97,11 +97,11 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-def philox4x64_10(ctr, key):
-    c = np.ascontiguousarray(ctr, dtype=np.uint64)
-    k = np.ascontiguousarray(key, dtype=np.uint64)
-    out = np.zeros(4, dtype=np.uint64)
-    lib().orc_philox4x64_10(_ptr(c), _ptr(k), _ptr(out))
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
 
 

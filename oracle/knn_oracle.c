@@ -7,7 +7,7 @@
  * the CUDA library.
  *
  * Pieces and where they come from:
- *   - Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
+ *   - Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw,
  *     "Parallel random numbers: as easy as 1, 2, 3", SC'11), written from the
  *     published round function.
  *   - coordinate draw: uniform index in [0, m) with replacement (Section 4,
@@ -40,41 +40,43 @@
 
 /* ---------------------------------------------------------------- Philox */
 
-static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
-    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
-    *hi = (uint64_t)(p >> 64);
-    *lo = (uint64_t)p;
-}
-
-void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
-    /* Multipliers and Weyl key increments of Philox4x64 (SC'11, Table 2). */
-    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
-    uint64_t k0 = key[0], k1 = key[1];
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    /* Multipliers and Weyl key increments of Philox4x32 (SC'11, Table 2):
+     * each round multiplies words 0 and 2, xors the high halves of the
+     * 64-bit products with the other words and the round key, and the key
+     * advances between rounds. */
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
     for (int round = 0; round < 10; ++round) {
         if (round > 0) { k0 += W0; k1 += W1; }
-        uint64_t hi0, lo0, hi1, lo1;
-        mulhilo64(M0, c0, &hi0, &lo0);
-        mulhilo64(M1, c2, &hi1, &lo1);
-        uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1, n3 = (uint32_t)p0;
         c0 = n0; c1 = n1; c2 = n2; c3 = n3;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* The s-th draw of a (query, point) pair: counter (s / 8, point, query, 0),
- * key (seed, 0); the 256 output bits are eight 32-bit words (low half of
- * each 64-bit word first) and word s mod 8 is scaled to [0, m) by
- * floor(word * m / 2^32). */
+/* Block `blk` of a (query, point) pair's stream: Philox4x32-10 at counter
+ * (blk, point, query low word, query high word), key (seed low word, seed
+ * high word). */
+static void pair_block(uint64_t seed, uint64_t qid, uint64_t point, uint32_t blk, uint64_t mask_p,
+                       uint64_t mask_q, uint32_t out[4]) {
+    const uint64_t qf = qid & mask_q;
+    uint32_t ctr[4] = {blk, (uint32_t)(point & mask_p), (uint32_t)qf, (uint32_t)(qf >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* The s-th draw of a (query, point) pair: word s mod 4 of block s / 4,
+ * scaled to [0, m) by floor(word * m / 2^32). */
 int32_t orc_coordinate(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
                        uint64_t mask_p, uint64_t mask_q) {
-    uint64_t ctr[4] = {s >> 3, point & mask_p, qid & mask_q, 0};
-    uint64_t key[2] = {seed, 0};
-    uint64_t out[4];
-    orc_philox4x64_10(ctr, key, out);
-    unsigned w = (unsigned)(s & 7);
-    uint32_t word = (uint32_t)(out[w >> 1] >> (32 * (w & 1)));
+    uint32_t out[4];
+    pair_block(seed, qid, point, (uint32_t)(s >> 2), mask_p, mask_q, out);
+    uint32_t word = out[s & 3];
     return (int32_t)(((uint64_t)word * (uint64_t)(uint32_t)m) >> 32);
 }
 
@@ -104,12 +106,10 @@ static uint32_t feistel8(uint32_t x, int h, const uint32_t k[8]) {
 
 int32_t orc_coordinate_wor(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
                            uint64_t mask_p, uint64_t mask_q) {
-    uint64_t ctr[4] = {~(uint64_t)0, point & mask_p, qid & mask_q, 0};
-    uint64_t key[2] = {seed, 0};
-    uint64_t out[4];
-    orc_philox4x64_10(ctr, key, out);
+    /* round keys: the two last blocks of the pair's stream */
     uint32_t k[8];
-    for (int r = 0; r < 8; ++r) k[r] = (uint32_t)(out[r >> 1] >> (32 * (r & 1)));
+    pair_block(seed, qid, point, 0xFFFFFFFEu, mask_p, mask_q, k);
+    pair_block(seed, qid, point, 0xFFFFFFFFu, mask_p, mask_q, k + 4);
     int bits = 0;
     while (((uint64_t)1 << bits) < (uint64_t)m) ++bits;  /* ceil(log2 m) */
     int h = (bits + 1) / 2;

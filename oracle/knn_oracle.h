@@ -25,20 +25,23 @@ enum { ORC_BOUND_FOOTNOTE = 0, ORC_BOUND_LEMMA = 1, ORC_BOUND_EXP = 2 };
 /* Per-point decision kinds written to the decision codes (code = 4*round + kind). */
 enum { ORC_ACTIVE = 0, ORC_ELIMINATED = 1, ORC_ACCEPTED = 2 };
 
-/* Philox4x64 with 10 rounds (Salmon et al., SC'11): out = philox(ctr, key). */
-void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+/* Philox4x32 with 10 rounds (Salmon et al., SC'11): out = philox(ctr, key). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
 /* Index in [0, m) of the s-th coordinate drawn (0-based) for point `point` of
- * query `qid`. Uniform with replacement (Section 4, sampled estimator). */
+ * query `qid`. Uniform with replacement (Section 4, sampled estimator): word
+ * s mod 4 of Philox4x32-10 at counter (s / 4, point & mask_p, low and high
+ * words of qid & mask_q), key (low and high words of seed), scaled to [0, m)
+ * by floor(word * m / 2^32). */
 int32_t orc_coordinate(uint64_t seed, uint64_t qid, uint64_t point, uint64_t s, int32_t m,
                        uint64_t mask_p, uint64_t mask_q);
 
 /* Without replacement (footnote to Section 4: a cipher on [m] makes the
  * estimate exact after m draws). The s-th draw (0-based, s < m) of a pair is
  * pi(s), pi a permutation of [0, m) keyed per (seed, point, query):
- *   round keys k_0..k_7 = the eight 32-bit words (low half of each 64-bit
- *   word first) of Philox4x64-10 at counter (2^64 - 1, point, query, 0),
- *   key (seed, 0); a balanced Feistel network (Luby and Rackoff) of 8 rounds
+ *   round keys k_0..k_7 = the words of blocks 2^32 - 2 and 2^32 - 1 of the
+ *   pair's Philox4x32-10 stream (counter and key as for orc_coordinate, in
+ *   that order); a balanced Feistel network (Luby and Rackoff) of 8 rounds
  *   on 2h bits (4 rounds leave consecutive draws visibly correlated on
  *   small domains),
  *   h = max(1, ceil(ceil(log2 m) / 2)): with x = (L, R), L the high h bits,

@@ -6,7 +6,7 @@
 // One CTA owns one query at a time and runs all of its rounds; CTAs take the
 // next query from a device work queue, so queries of uneven difficulty share
 // the GPU without host round trips. Per round and query:
-//   gather    every active point draws B_r coordinates (Philox4x64-10) and
+//   gather    every active point draws B_r coordinates (Philox4x32-10) and
 //             adds the squared differences to its FP32 Kahan sum S, or takes
 //             its exact distance once the count would reach m (Algorithm 1);
 //             the same pass histograms the new sums (bits 31..20 of the key);
@@ -216,11 +216,12 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
 // Draw s (< m) of a pair sampled without replacement (the footnote to
 // Section 4: a cipher on [m]): a balanced Feistel network of 8 rounds on 2h
 // bits (L the high h bits; a round maps (L, R) to (R, L ^ (fmix32(R ^ k_r) mod
-// 2^h))) keyed by the eight 32-bit words of the pair's Philox block k,
+// 2^h))) keyed by the eight words of the last two Philox blocks of the pair's
+// stream (k),
 // extended to [0, m) by cycle walking (apply it again until the value is
 // below m). From s < m the walk returns below m within one cycle of the
 // permutation of [0, 4^h); the walk is capped at 4^h steps all the same.
-__device__ __forceinline__ int wor_coordinate(const Philox4x64& k, uint32_t s, uint32_t m, int h) {
+__device__ __forceinline__ int wor_coordinate(const Draws8& k, uint32_t s, uint32_t m, int h) {
   const uint32_t mask = (1u << h) - 1u;
   const uint32_t cap = 1u << (2 * h);
   uint32_t x = s;
@@ -324,7 +325,7 @@ __device__ float kth_of_union(const float* A, int na, const float* Bv, int nb, i
 // Sampled gather: slots [0, nact) of the active list, samples T .. Tn-1.
 // G lanes share a point (G = blocks of 8 draws this round, rounded up to a
 // power of two, at most 32); each lane walks its blocks of its points as one
-// flat sequence of items and computes the next item's Philox block while the
+// flat sequence of items and computes the next item's Philox blocks while the
 // current item's 8 loads are in flight (software pipelining over items).
 template <int NT, class E, bool L1>
 __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
@@ -407,10 +408,9 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
   uint64_t b;
   bool has;
   item(0, sidx, id, b, has);
-  // (without replacement one block per pair: counter word 0 all ones, the round keys)
-  const uint64_t ctr0 = E::kWor ? ~0ull : 0ull;
-  Philox4x64 ph = has ? philox4x64_10(E::kWor ? ctr0 : b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0)
-                      : Philox4x64{};
+  // (without replacement one item per pair: the last two blocks of its stream, the round keys)
+  Draws8 ph = has ? pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.seed)
+                  : Draws8{};
   float part = 0.0f;
   for (int t = 0; t < nitems; ++t) {
     // issue the current item's loads
@@ -435,7 +435,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
     // the next item's Philox while the loads are in flight
     if (t + 1 < nitems) {
       item(t + 1, sidx, id, b, has);
-      if (has) ph = philox4x64_10(E::kWor ? ctr0 : b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0);
+      if (has) ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.seed);
     }
     // consume
     if (cur_has) {
@@ -506,7 +506,7 @@ __device__ __forceinline__ float block_sum32(const uint4 v0, const uint4 v1, con
 // Block samples (g > 1 coordinates per draw): draw s of a pair picks block
 // jb = floor(word_s * Mb / 2^32) and adds the squared differences of its
 // coordinates jb*g .. min(jb*g + g, m) - 1 in order. Lanes, items (one
-// Philox block of 8 draws) and the reduction are those of gather_sampled. A
+// two Philox blocks, 8 draws) and the reduction are those of gather_sampled. A
 // 32-byte block on 16-byte aligned rows (gvec) is two 16-byte loads, F draws
 // in flight per lane; a ragged last block is read element by element.
 template <int NT, class E, bool L1>
@@ -539,7 +539,7 @@ __device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qi
     const uint64_t b = blo + (uint64_t)(gl + jt * G);
     if (sidx < nact && b <= bhi) {
       const int id = (r == 0) ? sidx : idc[sidx];
-      const Philox4x64 ph = philox4x64_10(b, (uint64_t)id & a.mask_p, qfield, 0, a.seed, 0);
+      const Draws8 ph = pair_draws8((uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.seed);
       const Tp* xr = G0 + (size_t)id * (size_t)m;
       const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
       const int64_t s0 = (int64_t)(b << 3);
@@ -1123,7 +1123,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
       float part = 0.0f;
       if (pi < np && gl < nblk) {
         const uint64_t id = (uint64_t)(p0 + pi);
-        const Philox4x64 ph = philox4x64_10(E::kWor ? ~0ull : (uint64_t)gl, id & a.mask_p, qfield, 0, a.seed, 0);
+        const Draws8 ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)gl, id & a.mask_p, qfield, a.seed);
         const float* xr = rows + (size_t)pi * m;
         if constexpr (!E::kBlk) {
 #pragma unroll

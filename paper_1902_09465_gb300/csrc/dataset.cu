@@ -76,12 +76,12 @@ static __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t 
   if (lane == 0) atomicMax(emax_bits, __float_as_uint(e));
 }
 
-// Column of draw t under shared coordinates: Philox4x64-10 with key
-// (seed, 0) and counter (t / 8, 0, 0, 0), word t mod 8 scaled to [0, m).
+// Column of draw t under shared coordinates: word t mod 4 of Philox4x32-10
+// at counter (t / 4, 0, 0, 0), key (seed words), scaled to [0, m).
 static __global__ void shared_columns_kernel(uint64_t seed, int m, int32_t* jperm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= m) return;
-  const Philox4x64 ph = philox4x64_10((uint64_t)t >> 3, 0, 0, 0, seed, 0);
+  const Draws8 ph = pair_draws8((uint32_t)(t >> 3), 0, 0, seed);
   jperm[t] = (int32_t)__umulhi(philox_word(ph, t & 7), (uint32_t)m);
 }
 

@@ -1,5 +1,5 @@
 // knn_common.cuh -- device helpers shared by the kernels of the library:
-// the Philox4x64-10 generator, order-preserving float keys, block-wide scans
+// the Philox4x32-10 generator, order-preserving float keys, block-wide scans
 // and reductions, a shared-memory bitonic sort and a three-level radix select
 // of the smallest keys.
 #pragma once
@@ -15,68 +15,60 @@ constexpr int kSelCap = 4096;    // keys a select may finish on in shared memory
 constexpr int kHistBins = 4096;  // level-1 bins (key bits 31..20)
 
 // ----------------------------------------------------------------- Philox
-// Philox4x64 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): the round
-// multiplies words 0 and 2 by fixed odd constants, takes the 128-bit
-// products' halves, xors the high halves with the other words and the round
-// key, and bumps the key by the Weyl constants between rounds.
-struct Philox4x64 {
-  uint64_t v[4];
-};
-
-// Full 64 x 64 -> 128-bit product from 32-bit limbs (schoolbook, with the
-// carry chain in PTX): four 32-bit partial products, nine instructions for
-// both halves instead of separate 64-bit low and high multiplies.
-__device__ __forceinline__ void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
-  const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32);
-  const uint32_t bl = (uint32_t)b, bh = (uint32_t)(b >> 32);
-  uint32_t r0, r1, r2, r3;
-  asm("mul.lo.u32 %0, %4, %6;\n\t"
-      "mul.hi.u32 %1, %4, %6;\n\t"
-      "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
-      "madc.hi.u32 %2, %4, %7, 0;\n\t"
-      "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
-      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
-      "madc.hi.u32 %3, %5, %7, 0;\n\t"
-      "mad.lo.cc.u32 %2, %5, %7, %2;\n\t"
-      "addc.u32 %3, %3, 0;"
-      : "=&r"(r0), "=&r"(r1), "=&r"(r2), "=&r"(r3)
-      : "r"(al), "r"(ah), "r"(bl), "r"(bh));
-  *lo = ((uint64_t)r1 << 32) | r0;
-  *hi = ((uint64_t)r3 << 32) | r2;
-}
-
-__device__ __forceinline__ Philox4x64 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                                    uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): the round
+// multiplies words 0 and 2 by fixed odd constants, xors the high halves of
+// the 64-bit products with the other words and the round key, and bumps the
+// key by the Weyl constants between rounds. 32-bit products are native.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                               uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     if (r) {
       k0 += W0;
       k1 += W1;
     }
-    uint64_t hi0, lo0, hi1, lo1;
-    mulhilo64(M0, c0, &hi0, &lo0);
-    mulhilo64(M1, c2, &hi1, &lo1);
-    const uint64_t n0 = hi1 ^ c1 ^ k0;
-    const uint64_t n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
+    const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    c0 = hi1 ^ c1 ^ k0;
     c1 = lo1;
-    c2 = n2;
+    c2 = hi0 ^ c3 ^ k1;
     c3 = lo0;
   }
-  Philox4x64 o;
-  o.v[0] = c0;
-  o.v[1] = c1;
-  o.v[2] = c2;
-  o.v[3] = c3;
-  return o;
+  return make_uint4(c0, c1, c2, c3);
 }
 
-// 32-bit word w (0..7) of a block: low half of each 64-bit word first.
-__device__ __forceinline__ uint32_t philox_word(const Philox4x64& p, int w) {
-  return (uint32_t)(p.v[w >> 1] >> (32 * (w & 1)));
+// Draws 8i .. 8i + 7 of a (query, point) pair: the words of blocks 2i and
+// 2i + 1 of its stream -- Philox4x32-10 at counter (block, point field, low
+// and high words of the query field), key (low and high words of the seed).
+struct Draws8 {
+  uint32_t w[8];
+};
+
+__device__ __forceinline__ Draws8 pair_draws8(uint32_t item, uint64_t point_field, uint64_t query_field,
+                                              uint64_t seed) {
+  const uint32_t p = (uint32_t)point_field, ql = (uint32_t)query_field, qh = (uint32_t)(query_field >> 32);
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint4 a = philox4x32_10(2u * item, p, ql, qh, k0, k1);
+  const uint4 b = philox4x32_10(2u * item + 1u, p, ql, qh, k0, k1);
+  Draws8 d;
+  d.w[0] = a.x;
+  d.w[1] = a.y;
+  d.w[2] = a.z;
+  d.w[3] = a.w;
+  d.w[4] = b.x;
+  d.w[5] = b.y;
+  d.w[6] = b.z;
+  d.w[7] = b.w;
+  return d;
 }
+
+// Item whose two blocks are the last of a pair's stream (blocks 2^32 - 2 and
+// 2^32 - 1): the round keys of the draws without replacement.
+constexpr uint32_t kWorKeyItem = 0x7FFFFFFFu;
+
+__device__ __forceinline__ uint32_t philox_word(const Draws8& d, int w) { return d.w[w]; }
 
 // ------------------------------------------------------------------- keys
 // Unsigned keys whose integer order is the float order (-0 < +0; NaN sorts

@@ -1,6 +1,7 @@
 """Pins for the CPU oracle: each test checks it against something other than
-itself (numpy's Philox and sort, closed-form special cases, brute force,
-Theorem 1's guarantee, the coherent example of Section 4.2)."""
+itself (Philox4x32-10's published known answers and triton's implementation,
+numpy's sort, closed-form special cases, brute force, Theorem 1's guarantee,
+the coherent example of Section 4.2)."""
 
 import math
 
@@ -8,6 +9,7 @@ import numpy as np
 import pytest
 from scipy import stats
 
+import _philox_ref
 import oracle
 from paper_1902_09465_gb300 import synth
 
@@ -16,35 +18,60 @@ FULL = (1 << 64) - 1
 
 # ------------------------------------------------------------------ Philox
 
-def _numpy_philox(ctr, key):
-    """Philox4x64-10 block for counter `ctr` from numpy's bit generator, which
-    increments its 256-bit counter before producing a block."""
-    c = sum(int(v) << (64 * i) for i, v in enumerate(ctr))
-    c = (c - 1) % (1 << 256)
-    pre = np.array([(c >> (64 * i)) & FULL for i in range(4)], dtype=np.uint64)
-    g = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=pre)
-    return g.random_raw(4).astype(np.uint64)
+# Known-answer vectors of Philox4x32-10 published with the generator (Salmon
+# et al., SC'11, Random123 distribution): counter, key, output words.
+KAT = [
+    ([0, 0, 0, 0], [0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
+    ([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
+    ([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0],
+     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
+]
 
 
-@pytest.mark.parametrize("ctr,key", [
-    ([0, 0, 0, 0], [0, 0]),
-    ([1, 0, 0, 0], [0, 0]),
-    ([FULL, FULL, FULL, FULL], [FULL, FULL]),
-    ([0x243F6A8885A308D3, 0x13198A2E03707344, 0xA4093822299F31D0, 0x082EFA98EC4E6C89],
-     [0x452821E638D01377, 0xBE5466CF34E90C6C]),
-    ([7, 123456, 42, 0], [2019, 0]),
-])
-def test_philox_matches_numpy(ctr, key):
-    np.testing.assert_array_equal(oracle.philox4x64_10(ctr, key), _numpy_philox(ctr, key))
+@pytest.mark.parametrize("ctr,key,expected", KAT)
+def test_philox_known_answers(ctr, key, expected):
+    assert [int(v) for v in oracle.philox4x32_10(ctr, key)] == expected
 
 
-def test_coordinates_follow_numpy_stream():
-    seed, qid, point, m = 99, 3, 12345, 784
+def test_philox_matches_triton_interpreter():
+    """Triton's Philox4x32-10 (run on the CPU by its interpreter) on random
+    counters and keys: a second, independent implementation."""
+    import os
+    os.environ["TRITON_INTERPRET"] = "1"
+    triton = pytest.importorskip("triton")
+    tl = pytest.importorskip("triton.language")
+    torch = pytest.importorskip("torch")
+
+    @triton.jit
+    def blocks(out, seed, c0p, c1p, c2p, c3p, N: tl.constexpr):
+        i = tl.arange(0, N)
+        a, b, c, d = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i), 10)
+        tl.store(out + i * 4, a)
+        tl.store(out + i * 4 + 1, b)
+        tl.store(out + i * 4 + 2, c)
+        tl.store(out + i * 4 + 3, d)
+
+    g = np.random.default_rng(11)
+    for _ in range(3):
+        seed = int(g.integers(0, 1 << 63))
+        ctr = g.integers(0, 1 << 32, size=(16, 4), dtype=np.uint64).astype(np.uint32)
+        cols = [torch.from_numpy(np.ascontiguousarray(ctr[:, j])) for j in range(4)]
+        out = torch.zeros(64, dtype=torch.uint32)
+        blocks[(1,)](out, seed, *cols, 16)
+        got = out.numpy().reshape(16, 4)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for r in range(16):
+            np.testing.assert_array_equal(oracle.philox4x32_10(ctr[r], key), got[r])
+
+
+def test_coordinates_follow_the_documented_stream():
+    seed, qid, point, m = 99 + (7 << 40), 3 + (5 << 33), 12345, 784
     for s in range(0, 40):
-        blk = _numpy_philox([s >> 3, point, qid, 0], [seed, 0])
-        w = s & 7
-        word = (int(blk[w >> 1]) >> (32 * (w & 1))) & 0xFFFFFFFF
-        assert oracle.coordinate(seed, qid, point, s, m) == (word * m) >> 32
+        assert oracle.coordinate(seed, qid, point, s, m) == _philox_ref.scaled(seed, qid, point, s, m)
+    # masks clear the point and query fields of the counter
+    for s in range(8):
+        w = _philox_ref.word(seed, 0, 0, s)
+        assert oracle.coordinate(seed, qid, point, s, m, mask_p=0, mask_q=0) == (w * m) >> 32
 
 
 def test_coordinates_uniform():
@@ -205,8 +232,8 @@ def test_all_coordinates_gives_exact_result():
 
 
 def test_estimates_are_sample_means_of_drawn_coordinates():
-    """S is the sum of squared differences at the coordinates numpy's Philox
-    stream selects, for T samples (sampled estimator, Section 4)."""
+    """S is the sum of squared differences at the coordinates the documented
+    Philox4x32 stream selects, for T samples (sampled estimator, Section 4)."""
     X, Q, _ = synth.gaussian_planted(40, 64, 3, seed=4)
     p = _params(k=3, B0=8, B=8, c_alpha=1e-3, seed=11)
     r = oracle.adaptive(X, Q, p)
@@ -217,9 +244,7 @@ def test_estimates_are_sample_means_of_drawn_coordinates():
         else:
             js = []
             for s in range(T):
-                blk = _numpy_philox([s >> 3, i, 0, 0], [11, 0])
-                w = s & 7
-                js.append((((int(blk[w >> 1]) >> (32 * (w & 1))) & 0xFFFFFFFF) * 64) >> 32)
+                js.append(_philox_ref.scaled(11, 0, i, s, 64))
             js = np.array(js)
             exp = ((X[i, js].astype(np.float64) - Q[0, js].astype(np.float64)) ** 2).sum()
         assert r["S"][0, i] == pytest.approx(exp, rel=1e-12, abs=0)

@@ -1,6 +1,6 @@
 """Pins for the oracle's block samples (a sample is one of M = ceil(m/g)
 blocks of g consecutive coordinates; its value the block's sum of squared
-differences). Each test checks the oracle against numpy's Philox stream and
+differences). Each test checks the oracle against the documented Philox stream and
 block sums, the exact distance, Theorem 1's guarantee or the coherent example
 of Section 4.2 -- never against the oracle itself."""
 
@@ -8,22 +8,13 @@ import numpy as np
 import pytest
 from scipy import stats
 
+import _philox_ref
 import oracle
 from paper_1902_09465_gb300 import synth
 
-FULL = (1 << 64) - 1
-
-
 def _numpy_block(seed, qid, point, s, M):
-    """Block index of draw s from numpy's Philox4x64-10 (counter (s/8, point,
-    qid, 0), key (seed, 0); numpy increments its counter before a block)."""
-    c = sum(int(v) << (64 * i) for i, v in enumerate([s >> 3, point, qid, 0]))
-    c = (c - 1) % (1 << 256)
-    pre = np.array([(c >> (64 * i)) & FULL for i in range(4)], dtype=np.uint64)
-    blk = np.random.Philox(key=np.array([seed, 0], dtype=np.uint64), counter=pre).random_raw(4)
-    w = s & 7
-    word = (int(blk[w >> 1]) >> (32 * (w & 1))) & 0xFFFFFFFF
-    return (word * M) >> 32
+    """Block index of draw s of the documented Philox4x32 stream."""
+    return _philox_ref.scaled(seed, qid, point, s, M)
 
 
 def _p(**kw):
@@ -49,7 +40,7 @@ def test_all_blocks_give_the_exact_distance(m, g):
 
 @pytest.mark.parametrize("m,g", [(77, 8), (96, 16), (300, 32)])
 def test_estimates_are_sums_of_the_drawn_blocks(m, g):
-    """S is the sum, over the T blocks numpy's Philox stream selects, of the
+    """S is the sum, over the T blocks the documented Philox stream selects, of the
     block's squared differences; the last block of a ragged row is shorter."""
     M = -(-m // g)
     X, Q, _ = synth.gaussian_planted(40, m, 3, seed=9)

@@ -1,6 +1,6 @@
 """Pins for the oracle's l1 metric (Section 3 names l1 as the generalisation
 of the method): brute force against numpy, the exact cap, samples against
-numpy's Philox stream, the identity with squared l2 on +-1/2 data (where
+the documented Philox stream, the identity with squared l2 on +-1/2 data (where
 |d| = d^2), Theorem 1's containment, and a closed-form case that separates
 the l1 width span*alpha from the l2 width span^2*alpha."""
 
@@ -8,19 +8,12 @@ import numpy as np
 import pytest
 from scipy import stats
 
+import _philox_ref
 import oracle
 from paper_1902_09465_gb300 import synth
 
-FULL = (1 << 64) - 1
-
-
 def _coord(seed, qid, point, s, m):
-    c = sum(int(v) << (64 * i) for i, v in enumerate([s >> 3, point, qid, 0]))
-    c = (c - 1) % (1 << 256)
-    pre = np.array([(c >> (64 * i)) & FULL for i in range(4)], dtype=np.uint64)
-    blk = np.random.Philox(key=np.array([seed, 0], dtype=np.uint64), counter=pre).random_raw(4)
-    w = s & 7
-    return ((int(blk[w >> 1]) >> (32 * (w & 1))) & 0xFFFFFFFF) * m >> 32
+    return _philox_ref.scaled(seed, qid, point, s, m)
 
 
 def test_l1_brute_force_matches_numpy_with_ties():

@@ -82,7 +82,7 @@ def test_vanishing_bounds_stop_before_the_first_iteration(heaps):
     """With C_alpha -> 0 every bound is its estimate, and the estimates are in
     order, so the termination test holds at once: no iteration, one draw per
     point, and the k + h smallest single-draw estimates by (estimate, index)
-    (the draws are orc_coordinate's, pinned to numpy's Philox)."""
+    (the draws are orc_coordinate's, pinned to the documented Philox4x32 stream)."""
     n, m, k, h = 60, 50, 4, 3
     X, Q, _ = synth.gaussian_planted(n, m, k, seed=11)
     q = Q[0]
