@@ -101,6 +101,16 @@ typedef struct {
     int32_t sampling;   /* knn_sampling: KNN_SAMPLE_WITH (default) or KNN_SAMPLE_WITHOUT (single
                          * coordinates, the FP32 data; not with shared-coordinate copies, block
                          * samples, stored copies or knn_adaptive_noalloc: KNN_EINVAL) */
+    int32_t r0_tensor;  /* 1: under shared coordinates (dataset calls with knn_dataset_share's copies,
+                         * B0 <= 64, single coordinates, squared l2) round 0 is a tcgen05 contraction:
+                         * every pair's sum over the shared columns J is formed as
+                         * ||x_J - mu||^2 + ||q_J - mu||^2 - 2 (x_J - mu).(q_J - mu) with the centred
+                         * values split into three BF16 parts (FP32 accumulation in tensor memory),
+                         * mu a fixed centre; that sum (within a few units of FP32 roundoff of
+                         * (||x_J - mu||^2 + ||q_J - mu||^2), not of the sum itself) decides which
+                         * points the round-0 filter drops, and every kept point's sum is taken
+                         * again sample by sample before the round's decisions. 0 (default): the
+                         * sums are taken sample by sample for every point. Ignored elsewhere. */
 } knn_opts;
 
 void knn_opts_default(knn_opts* opts);

@@ -25,6 +25,7 @@ extern "C" void knn_opts_default(knn_opts* o) {
   o->block = 1;
   o->metric = KNN_METRIC_L2SQ;
   o->sampling = KNN_SAMPLE_WITH;
+  o->r0_tensor = 0;
 }
 
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {
@@ -40,6 +41,7 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
     cv.take<float>(chunk * (size_t)n);                                      // round-0 sums
     cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // their tile minima
     cv.take<float>(chunk * 64);                                             // permuted query columns
+    if (o.r0_tensor && o.B0 <= 64) cv.take<uint8_t>(round0_tc_scratch(n, (int32_t)chunk));  // tensor-core round 0
   }
   return cv.off + 256;
 }

@@ -94,6 +94,8 @@ struct AdaptiveArgs {
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
   unsigned long long* phase_clk;  // per-phase clock totals [16] (libraries built with phase timing; else null)
   int32_t wor_h;        // draws without replacement: half width h of the Feistel network (4^h >= m)
+  int32_t r0_resum = 0; // the round-0 sums came from the tensor-core contraction: the points the
+                        // round-0 filter keeps get their sums again, sample by sample
 };
 
 // Phase timing (compiled in only with KNN_PHASE_TIMING): thread 0 of each CTA
@@ -330,7 +332,7 @@ __device__ float kth_of_union(const float* A, int na, const float* Bv, int nb, i
 template <int NT, class E, bool L1>
 __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t qid, int r, int nact, int64_t T, int64_t Tn,
                                                const float* qs, const int32_t* idc, float* Sc, float* Cc,
-                                               uint32_t* hist) {
+                                               uint32_t* hist, bool ids_given = false) {
   using Tp = typename E::T;
   const int m = a.m;
   const uint64_t blo = (uint64_t)T >> 3, bhi = (uint64_t)(Tn - 1) >> 3;
@@ -348,7 +350,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
       const int sidx = base + grp;
       float part = 0.0f;
       if (sidx < nact) {
-        const int id = (r == 0) ? sidx : idc[sidx];
+        const int id = (r == 0 && !ids_given) ? sidx : idc[sidx];
         const Tp* xr = static_cast<const Tp*>(a.G) + (size_t)id * (size_t)a.mp;
         const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
         for (uint64_t b = blo + gl; b <= bhi; b += G) {
@@ -865,9 +867,19 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
       KNN_PHASE(0);  // setup
-      if (flt)
+      if (flt) {
         nact = round0_filter<NT>(a, q, n, k, w, Tf, hist, buf, sh, ids0 + (size_t)cur * n, Sc,
                                  ids0 + (size_t)(cur ^ 1) * n, S0 + (size_t)(cur ^ 1) * n, lcode, lS, &min_elim);
+        if constexpr (E::kPerm) {
+          if (a.r0_resum) {
+            // the contraction's sums only chose the points the filter keeps:
+            // their sums again, sample by sample, before the round's decisions
+            for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
+            __syncthreads();
+            gather_sampled<NT, E, L1>(a, qid, 0, nact, 0, Tn, qsp, idc, Sc, Cc, hist, true);
+          }
+        }
+      }
       else if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT, L1>(a, r, nact, qs, idc, Sc, hist);
       else if (pre)

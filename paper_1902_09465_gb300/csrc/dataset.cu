@@ -175,6 +175,8 @@ extern "C" knn_status knn_dataset_destroy(knn_dataset* ds) {
   cudaFree(ds->p32);
   cudaFree(ds->pb);
   cudaFree(ds->p8);
+  cudaFree(ds->r0mu);
+  for (int st = 0; st < 3; ++st) cudaFree(ds->r0op[st]);
   cudaSetDevice(cur);
   delete ds;
   return KNN_OK;
@@ -310,6 +312,11 @@ extern "C" knn_status knn_dataset_share(knn_dataset* ds, uint64_t seed, int32_t 
   if ((copies >> KNN_STORE_BF16) & 1) permute_rows_kernel<uint16_t><<<blocks, 256, 0, stream>>>(ds->xb, n, m, ds->mp, ds->jperm, ds->pb);
   if ((copies >> KNN_STORE_FP8) & 1) permute_rows_kernel<uint8_t><<<blocks, 256, 0, stream>>>(ds->x8, n, m, ds->mp, ds->jperm, ds->p8);
   s = cuda_check(cudaGetLastError(), "shared-coordinate kernels");
+  // the round-0 contraction's operands (centre recomputed for this seed's columns)
+  cudaFree(ds->r0mu);
+  ds->r0mu = nullptr;
+  for (int st = 0; st < 3 && s == KNN_OK; ++st)
+    if ((copies >> st) & 1) s = build_round0_operand(ds, st, stream);
   if (s == KNN_OK) s = cuda_check(cudaStreamSynchronize(stream), "shared-coordinate build");
   if (s == KNN_OK) {
     ds->share_seed = seed;

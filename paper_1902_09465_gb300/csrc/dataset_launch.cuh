@@ -37,10 +37,13 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
   const int qpw = E::kPerm && r0 ? (o.B0 <= 16 ? 16 : (o.B0 <= 32 ? 32 : 64)) : 0;  // staged by round 0
+  // round 0 under shared coordinates as a tensor-core contraction (squared l2)
+  const bool r0tc = E::kPerm && r0 && o.r0_tensor && o.metric == KNN_METRIC_L2SQ && ds->r0op[E::kStorage];
   if (r0) {
     measure.take<float>((size_t)chunk * (size_t)n);
     measure.take<float>((size_t)chunk * (size_t)tiles);
     measure.take<float>((size_t)chunk * (size_t)qpw);
+    if (r0tc) measure.take<uint8_t>(round0_tc_scratch(n, chunk));
   }
   const size_t need = measure.off + 256;
   Workspace ws;
@@ -53,6 +56,7 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   float* r0buf = r0 ? cv.take<float>((size_t)chunk * (size_t)n) : nullptr;
   float* r0min = r0 ? cv.take<float>((size_t)chunk * (size_t)tiles) : nullptr;
   float* qperm = qpw ? cv.take<float>((size_t)chunk * (size_t)qpw) : nullptr;
+  uint8_t* r0scratch = r0tc ? cv.take<uint8_t>(round0_tc_scratch(n, chunk)) : nullptr;
   AdaptiveArgs a;
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
@@ -115,6 +119,7 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   a.jperm = ds->jperm;
   a.mp = ds->mp;
   a.phase_clk = phase_clocks_ptr();
+  a.r0_resum = r0tc ? 1 : 0;
   if (r0 && !E::kPerm) {
     s = cuda_check(cudaFuncSetAttribute(a.l1 ? reinterpret_cast<const void*>(round0_kernel<E, true>)
                                              : reinterpret_cast<const void*>(round0_kernel<E, false>),
@@ -142,7 +147,9 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
     ac.qid_base = a.qid_base + (uint64_t)q0;
     s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
     if (r0) kernel_mark(stream, 0);
-    if (s == KNN_OK && r0) {
+    if (s == KNN_OK && r0tc) {
+      s = round0_tc(ds, E::kStorage, ac.Q, ac.nq, o.B0, r0buf, r0min, tiles, r0scratch, stream);
+    } else if (s == KNN_OK && r0) {
       if constexpr (E::kPerm) {
         const unsigned blocks = (unsigned)((n + kR0SharedThreads - 1) / kR0SharedThreads);
         const int64_t cnt = (int64_t)ac.nq * qpw;

@@ -63,6 +63,16 @@ struct SymbolSlot {
 };
 knn_status symbol_address(const void* symbol, SymbolSlot (&slots)[64], void** out, const char* what);
 
+// Round 0 under shared coordinates as a tcgen05 contraction (screen_tc.cu):
+// writes R0[q * n + i] = sum_{t < B0} (x_it - q_t)^2 over the first B0
+// permuted columns (as ||xc||^2 + ||qc||^2 - 2 xc.qc of centred values, FP32)
+// and R0min[q * r0tiles + i / 32] = the smallest sum of each group of 32
+// points, for the nq queries of Q (the chunk).
+knn_status round0_tc(const knn_dataset* ds, int storage, const float* Q, int32_t nq, int32_t B0, float* R0,
+                     float* R0min, int32_t r0tiles, void* scratch, cudaStream_t stream);
+size_t round0_tc_scratch(int64_t n, int32_t nq);
+knn_status build_round0_operand(knn_dataset* ds, int storage, cudaStream_t stream);
+
 // Library status word of the current device: kernels that give up a bounded
 // wait record a code here (read and cleared by knn_device_status).
 knn_status device_status_ptr(int** out);
@@ -110,4 +120,8 @@ struct knn_dataset {
   float* p32 = nullptr;
   uint16_t* pb = nullptr;
   uint8_t* p8 = nullptr;
+  // tensor-core operand of the shared round 0, per storage: the first 64
+  // permuted columns minus r0mu, split into three BF16 parts [hi | mid | lo]
+  float* r0mu = nullptr;
+  uint16_t* r0op[3] = {nullptr, nullptr, nullptr};
 };

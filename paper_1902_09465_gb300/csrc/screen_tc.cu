@@ -40,6 +40,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -225,6 +226,10 @@ struct ScreenArgs {
   float* cand_d;      // pass 2: [nq][cap] their screened values D~
   int cap;
   int* status;        // library status word
+  int ksteps;         // MMAs (K = 16 each) per stage: 4, or fewer when the operands' columns end earlier
+  int8_t akb[8];      // pass 3: K block of A and of B loaded by stage kb (part products of split operands)
+  int8_t bkb[8];
+  float* r0;          // pass 3: [nq][n] the round-0 sums (gmin takes the group minima)
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -285,8 +290,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           mbar_expect_tx(full0 + 8 * s, kTcABytes + kTcBBytes);
-          tma_load_2d(smem_u32(sA + s * kTcABytes), &mapA, full0 + 8 * s, kb * kTcK, p0);
-          tma_load_2d(smem_u32(sB + s * kTcBBytes), &mapB, full0 + 8 * s, kb * kTcK, q0);
+          const int ka = a.pass == 3 ? a.akb[kb] : kb, kbb = a.pass == 3 ? a.bkb[kb] : kb;
+          tma_load_2d(smem_u32(sA + s * kTcABytes), &mapA, full0 + 8 * s, ka * kTcK, p0);
+          tma_load_2d(smem_u32(sB + s * kTcBBytes), &mapB, full0 + 8 * s, kbb * kTcK, q0);
           issued = it + 1;
         }
       }
@@ -315,8 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           tc_fence_after();
           const uint64_t ad = sw128_kmajor_desc(smem_u32(sA + s * kTcABytes));
           const uint64_t bd = sw128_kmajor_desc(smem_u32(sB + s * kTcBBytes));
-#pragma unroll
-          for (int ks = 0; ks < kTcK / 16; ++ks)  // 16 elements = 32 bytes per step along K
+          for (int ks = 0; ks < a.ksteps; ++ks)  // 16 elements = 32 bytes per step along K
             umma_f16kind(d, ad + 2 * ks, bd + 2 * ks, a.idesc, (kb | ks) != 0);
           umma_commit(empty0 + 8 * s);
         }
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       {  // the tile's per-column constants: ||qc||^2 and the cut (-inf: no query)
         const int q = q0 + et;
         colv[et] = q < a.nq ? make_float2(__ldg(a.qn + q), a.pass == 2 ? __ldg(a.cut + q) : 0.0f)
-                            : make_float2(0.0f, -INFINITY);
+                            : make_float2(0.0f, -INFINITY);  // (passes 1 and 3: 0 marks a query)
       }
       epi_sync();
       const uint32_t taddr =
@@ -362,19 +367,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         float v[32];
         tmem_ld_x32(taddr + (uint32_t)c0, v);
         const int cb = half * (kTcN / 2) + c0;  // tile column of v[0]
-        if (a.pass == 1) {
+        if (a.pass != 2) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float2 cv = colv[cb + j];
             v[j] = cv.y == -INFINITY ? INFINITY : fmaf(c2, v[j], xv + cv.x);
+          }
+          if (a.pass == 3 && p < a.n) {  // round-0 sums: a sum of squares is never below 0
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              v[j] = fmaxf(v[j], 0.0f);
+              const int q = q0 + cb + j;
+              if (q < a.nq) a.r0[(size_t)q * a.n + p] = v[j];
+            }
           }
           const float mn0 = warp_min16(*reinterpret_cast<float(*)[16]>(v), lane);
           const float mn1 = warp_min16(*reinterpret_cast<float(*)[16]>(v + 16), lane);
           if ((lane & 1) == 0) {
             const size_t unit = (size_t)pt_vis * 4 + quarter;
             const int qa = q0 + cb + (lane >> 1), qb = qa + 16;
-            if (qa < a.nq) a.gmin[(size_t)qa * a.nunits + unit] = mn0;
-            if (qb < a.nq) a.gmin[(size_t)qb * a.nunits + unit] = mn1;
+            if (unit < (size_t)a.nunits) {  // (round 0: groups past the last point are not stored)
+              if (qa < a.nq) a.gmin[(size_t)qa * a.nunits + unit] = mn0;
+              if (qb < a.nq) a.gmin[(size_t)qb * a.nunits + unit] = mn1;
+            }
           }
         } else {
           uint32_t hit = 0;
@@ -795,6 +810,7 @@ knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32
   a.cand_d = c.cand_d;
   a.cap = kScreenCap;
   a.status = status;
+  a.ksteps = kTcK / 16;
 
   // pass 1: group minima over every s-th point tile (skipped when every
   // point fits the candidate list: the cut is then +inf)
@@ -844,6 +860,227 @@ knn_status exact_tc(const knn_dataset* ds, int32_t screen, const float* Q, int32
                       c.cand_d, c.eq);
   ws.release();
   return s;
+}
+
+// ---- round 0 under shared coordinates as a tensor-core contraction
+
+constexpr int kR0Cols = 64;  // permuted columns held by the operand (B0 <= 64)
+
+// Three BF16 parts of an FP32 value: v = hi + mid + lo exactly for normal v
+// (each part takes the next 8 significant bits, rounded to nearest).
+__device__ __forceinline__ void split3(float v, uint16_t* h, uint16_t* m, uint16_t* l) {
+  const __nv_bfloat16 a = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(a);
+  const __nv_bfloat16 b = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(b);
+  *h = __bfloat16_as_ushort(a);
+  *m = __bfloat16_as_ushort(b);
+  *l = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+
+// Centre of the operand: the mean of each of the first 64 permuted columns
+// of the FP32 data (any fixed vector works; this one keeps the centred
+// values, and the cancellation in ||xc||^2 + ||qc||^2 - 2 xc.qc, small).
+static __global__ void r0_centre_kernel(const float* __restrict__ X, int64_t n, int m,
+                                        const int32_t* __restrict__ jperm, int cols, float* __restrict__ mu) {
+  const int t = threadIdx.x;
+  if (t >= cols) return;
+  const int j = jperm[t];
+  float s = 0.0f;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) s += __ldg(X + (size_t)i * m + j);
+  atomicAdd(&mu[t], s);
+}
+
+// Operand rows [hi | mid | lo] (64 columns each) of v - mu, v the value of the
+// gathered copy at permuted column t (dequantised for FP8), zero past m and
+// for padding rows.
+template <int Storage>
+static __global__ void r0_operand_kernel(const void* __restrict__ G, const float* __restrict__ scale8, int64_t n,
+                                         int64_t rows_pad, int m, int mp, const float* __restrict__ mu,
+                                         uint16_t* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows_pad * kR0Cols) return;
+  const int64_t i = e / kR0Cols;
+  const int t = (int)(e - i * kR0Cols);
+  float v = 0.0f;
+  if (i < n && t < m) {
+    float x;
+    if (Storage == KNN_STORE_F32) {
+      x = __ldg(static_cast<const float*>(G) + (size_t)i * mp + t);
+    } else if (Storage == KNN_STORE_BF16) {
+      x = __uint_as_float((uint32_t)__ldg(static_cast<const uint16_t*>(G) + (size_t)i * mp + t) << 16);
+    } else {
+      __nv_fp8_e4m3 f;
+      f.__x = __ldg(static_cast<const uint8_t*>(G) + (size_t)i * mp + t);
+      x = __fmul_rn(static_cast<float>(f), __ldg(scale8 + i));
+    }
+    v = x - mu[t];
+  }
+  uint16_t h, md, l;
+  split3(v, &h, &md, &l);
+  uint16_t* o = out + (size_t)i * 3 * kR0Cols;
+  o[t] = h;
+  o[kR0Cols + t] = md;
+  o[2 * kR0Cols + t] = l;
+}
+
+knn_status build_round0_operand(knn_dataset* ds, int storage, cudaStream_t stream) {
+  const int64_t n = ds->n;
+  const int64_t rows_pad = (n + kTcM - 1) / kTcM * kTcM;
+  knn_status s = KNN_OK;
+  if (!ds->r0mu) {
+    s = cuda_check(cudaMalloc(&ds->r0mu, kR0Cols * 4), "cudaMalloc(round-0 centre)");
+    if (s == KNN_OK) s = cuda_check(cudaMemsetAsync(ds->r0mu, 0, kR0Cols * 4, stream), "memset");
+    if (s != KNN_OK) return s;
+    DeviceInfo di;
+    s = device_info(&di);
+    if (s != KNN_OK) return s;
+    const int cols = std::min(kR0Cols, ds->m);
+    r0_centre_kernel<<<di.sms * 4, kR0Cols, 0, stream>>>(ds->X, n, ds->m, ds->jperm, cols, ds->r0mu);
+    scale_kernel<<<1, kR0Cols, 0, stream>>>(ds->r0mu, kR0Cols, 1.0f / (float)n);
+    s = cuda_check(cudaGetLastError(), "round-0 centre");
+    if (s != KNN_OK) return s;
+  }
+  if (!ds->r0op[storage])
+    s = cuda_check(cudaMalloc(&ds->r0op[storage], (size_t)rows_pad * 3 * kR0Cols * 2), "cudaMalloc(round-0 operand)");
+  if (s != KNN_OK) return s;
+  const int64_t count = rows_pad * kR0Cols;
+  const unsigned blocks = (unsigned)((count + 255) / 256);
+  if (storage == KNN_STORE_F32)
+    r0_operand_kernel<KNN_STORE_F32><<<blocks, 256, 0, stream>>>(ds->p32, ds->scale8, n, rows_pad, ds->m, ds->mp,
+                                                                 ds->r0mu, ds->r0op[storage]);
+  else if (storage == KNN_STORE_BF16)
+    r0_operand_kernel<KNN_STORE_BF16><<<blocks, 256, 0, stream>>>(ds->pb, ds->scale8, n, rows_pad, ds->m, ds->mp,
+                                                                  ds->r0mu, ds->r0op[storage]);
+  else
+    r0_operand_kernel<KNN_STORE_FP8><<<blocks, 256, 0, stream>>>(ds->p8, ds->scale8, n, rows_pad, ds->m, ds->mp,
+                                                                 ds->r0mu, ds->r0op[storage]);
+  return cuda_check(cudaGetLastError(), "round-0 operand");
+}
+
+// Query side: rows [hi | mid | lo] of q_(jperm t) - mu_t for t < B0 (zero past
+// B0 and for padding rows), and ||qc||^2 over those B0 columns (FP32, the
+// parts summed back exactly).
+static __global__ void r0_query_kernel(const float* __restrict__ Q, int nq, int64_t nq_pad, int m,
+                                       const int32_t* __restrict__ jperm, const float* __restrict__ mu, int B0,
+                                       uint16_t* __restrict__ out, float* __restrict__ qn) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= nq_pad) return;
+  float sq = 0.0f;
+  for (int t = lane; t < kR0Cols; t += 32) {
+    float v = 0.0f;
+    if (q < nq && t < B0) v = __ldg(Q + (size_t)q * m + jperm[t]) - mu[t];
+    uint16_t h, md, l;
+    split3(v, &h, &md, &l);
+    uint16_t* o = out + (size_t)q * 3 * kR0Cols;
+    o[t] = h;
+    o[kR0Cols + t] = md;
+    o[2 * kR0Cols + t] = l;
+    sq = fmaf(v, v, sq);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0 && q < nq) qn[q] = sq;
+}
+
+// ||xc||^2 over the first B0 permuted columns of each point, from its parts.
+static __global__ void r0_point_norms_kernel(const uint16_t* __restrict__ op, int64_t n, int B0,
+                                             float* __restrict__ xn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint16_t* o = op + (size_t)i * 3 * kR0Cols;
+  float s = 0.0f;
+  for (int t = 0; t < B0; ++t) {
+    const float v = (__uint_as_float((uint32_t)o[t] << 16) + __uint_as_float((uint32_t)o[kR0Cols + t] << 16)) +
+                    __uint_as_float((uint32_t)o[2 * kR0Cols + t] << 16);
+    s = fmaf(v, v, s);
+  }
+  xn[i] = s;
+}
+
+static __global__ void fill_kernel(float* p, float v) { *p = v; }
+
+struct R0Carve {
+  uint16_t* B;
+  float* qn;
+  float* xn;
+  float* c2;
+};
+
+static size_t carve_r0(Carve& cv, int64_t n, int32_t nq, R0Carve* out) {
+  R0Carve c;
+  const size_t nq_pad = (size_t)((nq + kTcN - 1) / kTcN) * kTcN;
+  c.B = cv.take<uint16_t>(nq_pad * 3 * kR0Cols);
+  c.qn = cv.take<float>(nq_pad);
+  c.xn = cv.take<float>((size_t)n);
+  c.c2 = cv.take<float>(1);
+  if (out) *out = c;
+  return cv.off;
+}
+
+size_t round0_tc_scratch(int64_t n, int32_t nq) {
+  Carve cv;
+  return carve_r0(cv, n, nq, nullptr) + 256;
+}
+
+knn_status round0_tc(const knn_dataset* ds, int storage, const float* Q, int32_t nq, int32_t B0, float* R0,
+                     float* R0min, int32_t r0tiles, void* scratch, cudaStream_t stream) {
+  const uint16_t* A = ds->r0op[storage];
+  if (!A || !ds->r0mu) return set_error("round0_tc: no round-0 operand for this storage"), KNN_EINVAL;
+  if (B0 < 1 || B0 > kR0Cols) return set_error("round0_tc: needs 1 <= B0 <= 64"), KNN_EINVAL;
+  DeviceInfo di;
+  knn_status s = device_info(&di);
+  if (s != KNN_OK) return s;
+  const int64_t n = ds->n;
+  const int64_t npt = (n + kTcM - 1) / kTcM;
+  const int64_t nq_pad = (int64_t)((nq + kTcN - 1) / kTcN) * kTcN;
+  Carve cv;
+  cv.base = reinterpret_cast<uint8_t*>(((uintptr_t)scratch + 255) & ~uintptr_t(255));
+  R0Carve c;
+  carve_r0(cv, n, nq, &c);
+  r0_query_kernel<<<(unsigned)((nq_pad + 7) / 8), 256, 0, stream>>>(Q, nq, nq_pad, ds->m, ds->jperm, ds->r0mu, B0,
+                                                                    c.B, c.qn);
+  r0_point_norms_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(A, n, B0, c.xn);
+  fill_kernel<<<1, 1, 0, stream>>>(c.c2, -2.0f);
+  s = cuda_check(cudaGetLastError(), "round-0 operand kernels");
+  CUtensorMap mapA, mapB;
+  if (s == KNN_OK) s = make_map(&mapA, A, npt * kTcM, 3 * kR0Cols, kTcM, true);
+  if (s == KNN_OK) s = make_map(&mapB, c.B, nq_pad, 3 * kR0Cols, kTcN, true);
+  int* status = nullptr;
+  if (s == KNN_OK) s = device_status_ptr(&status);
+  const size_t smem = screen_smem_bytes();
+  if (s == KNN_OK)
+    s = cuda_check(cudaFuncSetAttribute(screen_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                   "cudaFuncSetAttribute(screen_tc)");
+  if (s != KNN_OK) return s;
+  ScreenArgs a{};
+  a.n = n;
+  a.nq = nq;
+  // xc.qc from the parts: hi.hi, hi.mid, hi.lo, mid.hi, mid.mid, lo.hi (the
+  // three dropped products are below 2^-26 |xc| |qc| together)
+  const int8_t akb[6] = {0, 0, 0, 1, 1, 2}, bkb[6] = {0, 1, 2, 0, 1, 0};
+  a.nk = 6;
+  for (int i = 0; i < 6; ++i) {
+    a.akb[i] = akb[i];
+    a.bkb[i] = bkb[i];
+  }
+  a.ksteps = (B0 + 15) / 16;
+  a.nqt = (int)(nq_pad / kTcN);
+  a.stride = 1;
+  a.ntiles = (int)(npt * a.nqt);
+  a.pass = 3;
+  a.idesc = idesc_f16kind(true);
+  a.limit = g_wait_limit.load();
+  a.xn = c.xn;
+  a.qn = c.qn;
+  a.c2 = c.c2;
+  a.gmin = R0min;
+  a.nunits = r0tiles;
+  a.r0 = R0;
+  a.status = status;
+  screen_tc_kernel<<<std::min(a.ntiles, di.sms), kTcThreads, smem, stream>>>(mapA, mapB, a);
+  return cuda_check(cudaGetLastError(), "screen_tc_kernel launch (round 0)");
 }
 
 }  // namespace knn

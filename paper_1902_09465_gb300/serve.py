@@ -69,6 +69,7 @@ class DatasetConfig:
     threads: int = 512
     bound: str = "exp"
     share: bool = False      # shared coordinates: both Philox masks zero, column-permuted copy
+    r0_tensor: bool = False  # with share: round 0 as a tensor-core contraction (knn_opts.r0_tensor)
     replace: bool = True     # False: each pair's draws without replacement (FP32 storage, no sharing)
     method: str = "adaptive"  # or "exact": screen GEMM + select + FP64 rerank (k_max of the batch)
 
@@ -116,7 +117,7 @@ class Server:
         c = self.configs[d]
         o = dict(bound=c.bound, c_alpha=c.c_alpha, B0=c.B0, B=c.B, grow=c.grow, threads=c.threads)
         if c.share:
-            o.update(share_points=True, share_queries=True)
+            o.update(share_points=True, share_queries=True, r0_tensor=c.r0_tensor)
         if not c.replace:
             o["replace"] = False
         return o

@@ -28,7 +28,8 @@ def _args(**kw):
 
 def test_phase_shares_and_gather_rate(monkeypatch):
     monkeypatch.setattr(bench, "kernel_sources_sha1", lambda: bench.TRAFFIC_CAPTURE["sha1"])
-    cfg = bench.TRAFFIC_CAPTURE["config"]
+    rec = bench.TRAFFIC_CAPTURE["records"][0]
+    cfg = rec["config"]
     opts = {key: cfg[key] for key in ("c_alpha", "B0", "B", "grow", "threads")}
     w = dict(bench.WORKLOAD, nq=cfg["nq"])
     out = bench.phase_report(_clk(600, 200, 100), opts, _args(), w)
@@ -36,17 +37,16 @@ def test_phase_shares_and_gather_rate(monkeypatch):
     assert sh["rounds"]["gather"] == pytest.approx(600 / 1000) and sh["round0"]["gather"] == pytest.approx(0.1)
     assert out["phase_clocks_total"] == 1000
     g = out["gather_phase_dram"]
-    rec = bench.TRAFFIC_CAPTURE
     want = (rec["rounds_bytes"] - 4.0 * w["n"] * w["nq"]) / (rec["rounds_ms"] * 1e-3 * 0.8) / 1e9
     assert g["share"] == pytest.approx(0.8) and g["gbs_at_least"] == pytest.approx(want, rel=1e-3)
     assert g["frac_at_least"] == pytest.approx(want / g["peak"], rel=1e-3)
 
 
-@pytest.mark.parametrize("change", [dict(opt="B0", val=16), dict(arg="storage", val="bf16"), dict(arg="share", val=True),
+@pytest.mark.parametrize("change", [dict(opt="B0", val=32), dict(arg="storage", val="bf16"), dict(arg="share", val=True),
                                     dict(arg="block", val=8), dict(w="nq", val=64), dict(sha="0" * 40)])
 def test_gather_rate_only_for_the_captured_configuration(change, monkeypatch):
     monkeypatch.setattr(bench, "kernel_sources_sha1", lambda: bench.TRAFFIC_CAPTURE["sha1"])
-    cfg = bench.TRAFFIC_CAPTURE["config"]
+    cfg = bench.TRAFFIC_CAPTURE["records"][0]["config"]
     opts = {key: cfg[key] for key in ("c_alpha", "B0", "B", "grow", "threads")}
     w = dict(bench.WORKLOAD, nq=cfg["nq"])
     args = _args()
@@ -80,8 +80,7 @@ def test_kernel_hash_ignores_comments(tmp_path, monkeypatch):
 def test_oracle_schedule_follows_the_gpu_arm():
     line_cfg = {"workload": "w", "c_alpha": 3e-4, "B0": 16, "B": 16, "grow": 0, "threads_per_query": 1024}
     assert bench.oracle_schedule(_args(), line_cfg) == {"c_alpha": 3e-4, "B0": 16, "B": 16, "grow": 0}
-    rec = bench.TRAFFIC_CAPTURE["config"]
-    assert bench.oracle_schedule(_args()) == {key: rec[key] for key in ("c_alpha", "B0", "B", "grow")}
+    assert bench.oracle_schedule(_args()) == bench.REFERENCE_SCHEDULE
     assert bench.oracle_schedule(_args(B0=4, cpu_c_alpha=1e-2))["B0"] == 4
     assert bench.oracle_schedule(_args(B0=4, cpu_c_alpha=1e-2))["c_alpha"] == 1e-2
 
