@@ -157,6 +157,24 @@ __device__ __forceinline__ int next_pow2(int x) {
 // largest key up to a power of two, which must fit in the buffer).
 template <int NT>
 __device__ void bitonic_sort_keys(uint32_t* buf, int cnt) {
+  if (cnt <= 32) {  // one warp, in registers: no block barrier per stage
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      uint32_t v = lane < cnt ? buf[lane] : 0xFFFFFFFFu;
+#pragma unroll
+      for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          const uint32_t o = __shfl_xor_sync(0xffffffffu, v, stride);
+          const bool lower = (lane & stride) == 0, up = (lane & size) == 0;
+          v = (lower == up) ? min(v, o) : max(v, o);
+        }
+      }
+      buf[lane] = v;
+    }
+    __syncthreads();
+    return;
+  }
   const int P = next_pow2(cnt < 2 ? 2 : cnt);
   for (int i = cnt + threadIdx.x; i < P; i += NT) buf[i] = 0xFFFFFFFFu;
   __syncthreads();
@@ -226,7 +244,11 @@ __device__ void select_smallest(Get get, int N, int kk, uint32_t* hist, uint32_t
   int below = ss.below, inbin = ss.inbin;
   int shift = 20;
   uint32_t prefix = b1;
-  bool done = below + inbin <= kSelCap;
+  // finish in shared memory once the candidates fit; for small kk go on to
+  // finer levels until one warp can sort them (a histogram level costs a few
+  // barriers, a block-wide sort of thousands of keys dozens)
+  const int cap = kk <= 32 ? 32 : kSelCap;
+  bool done = below + inbin <= cap;
   if (!done) {
     // level 2: bits 19..10 of keys in bin b1
     for (int i = threadIdx.x; i < 1024; i += NT) hist[i] = 0;
@@ -242,7 +264,7 @@ __device__ void select_smallest(Get get, int N, int kk, uint32_t* hist, uint32_t
     inbin = ss.inbin;
     shift = 10;
     prefix = (b1 << 10) | b2;
-    done = below + inbin <= kSelCap;
+    done = below + inbin <= cap;
     if (!done) {
       // level 3: bits 9..0 of keys with prefix (b1, b2); fixes the key exactly
       for (int i = threadIdx.x; i < 1024; i += NT) hist[i] = 0;
