@@ -609,36 +609,50 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
                                              const int32_t* idc, float* Sc, uint32_t* hist) {
   const int m = a.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int sidx = warp; sidx < nact; sidx += NT / 32) {
-    const int id = (r == 0) ? sidx : idc[sidx];
-    const float* xr = a.X + (size_t)id * (size_t)m;
-    float part = 0.0f;
+  // two rows per warp at a time, their loads interleaved (each row's sum in
+  // the same order as one row alone)
+  for (int s0 = 2 * warp; s0 < nact; s0 += 2 * (NT / 32)) {
+    const bool two = s0 + 1 < nact;
+    const int ida = (r == 0) ? s0 : idc[s0];
+    const int idb = two ? ((r == 0) ? s0 + 1 : idc[s0 + 1]) : ida;
+    const float* xa = a.X + (size_t)ida * (size_t)m;
+    const float* xb = a.X + (size_t)idb * (size_t)m;
+    float pa = 0.0f, pb = 0.0f;
     if (a.vec) {
 #pragma unroll 4
       for (int j = lane * 4; j < m; j += 128) {
-        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr + j));
+        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xa + j));
+        const float4 y4 = __ldg(reinterpret_cast<const float4*>(xb + j));
         const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
-        float d = x4.x - q4.x;
-        part = add_term<L1>(d, part);
-        d = x4.y - q4.y;
-        part = add_term<L1>(d, part);
-        d = x4.z - q4.z;
-        part = add_term<L1>(d, part);
-        d = x4.w - q4.w;
-        part = add_term<L1>(d, part);
+        pa = add_term<L1>(x4.x - q4.x, pa);
+        pb = add_term<L1>(y4.x - q4.x, pb);
+        pa = add_term<L1>(x4.y - q4.y, pa);
+        pb = add_term<L1>(y4.y - q4.y, pb);
+        pa = add_term<L1>(x4.z - q4.z, pa);
+        pb = add_term<L1>(y4.z - q4.z, pb);
+        pa = add_term<L1>(x4.w - q4.w, pa);
+        pb = add_term<L1>(y4.w - q4.w, pb);
       }
     } else {
 #pragma unroll 4
       for (int j = lane; j < m; j += 32) {
-        const float d = __ldg(xr + j) - qs[j];
-        part = add_term<L1>(d, part);
+        const float qj = qs[j];
+        pa = add_term<L1>(__ldg(xa + j) - qj, pa);
+        pb = add_term<L1>(__ldg(xb + j) - qj, pb);
       }
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    for (int o = 16; o; o >>= 1) {
+      pa += __shfl_xor_sync(0xffffffffu, pa, o);
+      pb += __shfl_xor_sync(0xffffffffu, pb, o);
+    }
     if (lane == 0) {
-      Sc[sidx] = part;
-      atomicAdd(&hist[f2key(part) >> 20], 1u);
+      Sc[s0] = pa;
+      atomicAdd(&hist[f2key(pa) >> 20], 1u);
+      if (two) {
+        Sc[s0 + 1] = pb;
+        atomicAdd(&hist[f2key(pb) >> 20], 1u);
+      }
     }
   }
 }
