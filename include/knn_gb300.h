@@ -111,6 +111,11 @@ typedef struct {
                          * points the round-0 filter drops, and every kept point's sum is taken
                          * again sample by sample before the round's decisions. 0 (default): the
                          * sums are taken sample by sample for every point. Ignored elsewhere. */
+    int32_t query_order; /* 1 (default): dataset calls take the queries of a batch in a locality order
+                          * (a SimHash of each query: 16 signs of projections of the query minus the
+                          * batch mean), so queries near one another run at the same time and the rows
+                          * they keep active stay in L2; 0: batch order. Only the schedule changes: a
+                          * query's draws, decisions and result depend on its id, not its turn. */
 } knn_opts;
 
 void knn_opts_default(knn_opts* opts);

@@ -26,6 +26,7 @@ extern "C" void knn_opts_default(knn_opts* o) {
   o->metric = KNN_METRIC_L2SQ;
   o->sampling = KNN_SAMPLE_WITH;
   o->r0_tensor = 0;
+  o->query_order = 1;
 }
 
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {
@@ -42,6 +43,11 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
     cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // their tile minima
     cv.take<float>(chunk * 64);                                             // permuted query columns
     if (o.r0_tensor && o.B0 <= 64) cv.take<uint8_t>(round0_tc_scratch(n, (int32_t)chunk));  // tensor-core round 0
+  }
+  {  // the locality order of a chunk (dataset paths: chunks of round0_chunk queries, or the whole batch)
+    const size_t chunk = nq <= kOrderMax ? (size_t)nq : (size_t)round0_chunk(n, nq, p.grid);
+    if (o.query_order && chunk >= 2 && chunk <= (size_t)kOrderMax)
+      cv.take<uint8_t>(query_order_scratch(m, (int32_t)chunk));
   }
   return cv.off + 256;
 }

@@ -94,6 +94,7 @@ struct AdaptiveArgs {
   int32_t mp;           // row pitch of a shared-coordinate copy (m rounded up to 8)
   unsigned long long* phase_clk;  // per-phase clock totals [16] (libraries built with phase timing; else null)
   int32_t wor_h;        // draws without replacement: half width h of the Feistel network (4^h >= m)
+  const int32_t* qorder = nullptr;  // order in which CTAs take the queries (null: batch order)
   int32_t r0_resum = 0; // the round-0 sums came from the tensor-core contraction: the points the
                         // round-0 filter keeps get their sums again, sample by sample
 };
@@ -774,8 +775,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   for (;;) {
     if (tid == 0) sh.q = atomicAdd(a.queue, 1);
     __syncthreads();
-    const int q = sh.q;
-    if (q >= a.nq) break;
+    if (sh.q >= a.nq) break;
+    const int q = a.qorder ? a.qorder[sh.q] : sh.q;
     // this query's k, h and counter id (a mixed batch gives each query its own)
     const int k = a.kq ? max(1, min(a.kq[q], a.k)) : a.k;
     const int kh = k + (a.h_per_k ? k : a.h);
@@ -1098,6 +1099,98 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     }
     __syncthreads();
   }
+}
+
+// ---- locality order of a batch's queries
+// Queries close to one another keep most of the same points active after
+// round 0, so running them at the same time lets those rows stay in L2. The
+// key is a SimHash of the query: the signs of 16 projections of the query
+// minus the batch's mean onto fixed +-1 directions (bit of a hash of
+// (direction, column)); ties by index. Only the schedule changes: a query's
+// draws, decisions and result depend on its id, not on when it runs.
+constexpr int kOrderMax = 16384;  // queries ordered at once (larger chunks keep the batch order)
+
+// Column sums of the batch (mean zeroed first): 32 slices of rows in parallel.
+static __global__ void query_mean_kernel(const float* __restrict__ Q, int nq, int m, float* __restrict__ mean) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  float s = 0.0f;
+  for (int q = blockIdx.y; q < nq; q += gridDim.y) s += __ldg(Q + (size_t)q * m + j);
+  atomicAdd(&mean[j], s);
+}
+
+static __global__ void query_code_kernel(const float* __restrict__ Q, int nq, int m, const float* __restrict__ mean,
+                                         uint64_t* __restrict__ keys) {
+  const int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= nq) return;
+  const float inv_nq = 1.0f / (float)nq;
+  float acc[16];
+#pragma unroll
+  for (int b = 0; b < 16; ++b) acc[b] = 0.0f;
+  for (int j = lane; j < m; j += 32) {
+    const float v = __ldg(Q + (size_t)q * m + j) - mean[j] * inv_nq;
+    const uint32_t h = fmix32((uint32_t)j * 0x9E3779B9u + 0x7F4A7C15u);
+#pragma unroll
+    for (int b = 0; b < 16; ++b) acc[b] += ((h >> b) & 1u) ? v : -v;
+  }
+  uint32_t code = 0;
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    float t = acc[b];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    code |= (t > 0.0f ? 1u : 0u) << b;
+  }
+  if (lane == 0) keys[q] = ((uint64_t)code << 32) | (uint32_t)q;
+}
+
+// One CTA: bitonic sort of the keys in shared memory, the query order out.
+static __global__ void __launch_bounds__(1024) query_order_kernel(const uint64_t* __restrict__ keys, int nq,
+                                                                   int32_t* __restrict__ order) {
+  extern __shared__ uint64_t sk[];
+  int P = 2;
+  while (P < nq) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < nq ? keys[i] : ~0ull;
+  __syncthreads();
+  for (int size = 2; size <= P; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+        const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t a = sk[lo], b = sk[hi];
+        if ((b < a) == up) {
+          sk[lo] = b;
+          sk[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < nq; i += blockDim.x) order[i] = (int32_t)(uint32_t)sk[i];
+}
+
+static inline size_t query_order_scratch(int32_t m, int32_t nq) {
+  return ((size_t)m * 4 + 255) / 256 * 256 + ((size_t)nq * 8 + 255) / 256 * 256 + ((size_t)nq * 4 + 255) / 256 * 256;
+}
+
+// The chunk's order into `order` (nq entries) from scratch of query_order_scratch bytes.
+static inline knn_status launch_query_order(const float* Q, int nq, int m, uint8_t* scratch, int32_t* order,
+                                            cudaStream_t stream) {
+  float* mean = reinterpret_cast<float*>(scratch);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(scratch + ((size_t)m * 4 + 255) / 256 * 256);
+  knn_status s0 = cuda_check(cudaMemsetAsync(mean, 0, (size_t)m * 4, stream), "memset(query mean)");
+  if (s0 != KNN_OK) return s0;
+  query_mean_kernel<<<dim3((m + 255) / 256, 32), 256, 0, stream>>>(Q, nq, m, mean);
+  query_code_kernel<<<(nq * 32 + 255) / 256, 256, 0, stream>>>(Q, nq, m, mean, keys);
+  int P = 2;
+  while (P < nq) P <<= 1;
+  const size_t smem = (size_t)P * 8;
+  knn_status s = cuda_check(
+      cudaFuncSetAttribute(query_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+      "cudaFuncSetAttribute(query order)");
+  if (s != KNN_OK) return s;
+  query_order_kernel<<<1, 1024, smem, stream>>>(keys, nq, order);
+  return cuda_check(cudaGetLastError(), "query order kernels");
 }
 
 // Round 0 for every query of a batch, point-major: a CTA stages a tile of

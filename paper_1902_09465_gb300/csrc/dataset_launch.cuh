@@ -45,6 +45,8 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
     measure.take<float>((size_t)chunk * (size_t)qpw);
     if (r0tc) measure.take<uint8_t>(round0_tc_scratch(n, chunk));
   }
+  const bool order = o.query_order && chunk >= 2 && chunk <= kOrderMax;
+  if (order) measure.take<uint8_t>(query_order_scratch(m, chunk));
   const size_t need = measure.off + 256;
   Workspace ws;
   s = ws.acquire(workspace, workspace_bytes, need, stream);
@@ -57,6 +59,10 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   float* r0min = r0 ? cv.take<float>((size_t)chunk * (size_t)tiles) : nullptr;
   float* qperm = qpw ? cv.take<float>((size_t)chunk * (size_t)qpw) : nullptr;
   uint8_t* r0scratch = r0tc ? cv.take<uint8_t>(round0_tc_scratch(n, chunk)) : nullptr;
+  uint8_t* oscratch = order ? cv.take<uint8_t>(query_order_scratch(m, chunk)) : nullptr;
+  int32_t* qorder = order ? reinterpret_cast<int32_t*>(oscratch + query_order_scratch(m, chunk) -
+                                                       ((size_t)chunk * 4 + 255) / 256 * 256)
+                          : nullptr;
   AdaptiveArgs a;
   const void* G = ds->X;
   if (E::kStorage == KNN_STORE_BF16) G = ds->xb;
@@ -146,6 +152,10 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
     ac.qids = a.qids ? a.qids + q0 : nullptr;
     ac.qid_base = a.qid_base + (uint64_t)q0;
     s = cuda_check(cudaMemsetAsync(c.queue, 0, 4, stream), "memset(queue)");
+    if (s == KNN_OK && order && ac.nq >= 2) {  // the chunk's locality order (before the round-0 pass)
+      s = launch_query_order(ac.Q, ac.nq, m, oscratch, qorder, stream);
+      ac.qorder = qorder;
+    }
     if (r0) kernel_mark(stream, 0);
     if (s == KNN_OK && r0tc) {
       s = round0_tc(ds, E::kStorage, ac.Q, ac.nq, o.B0, r0buf, r0min, tiles, r0scratch, stream);

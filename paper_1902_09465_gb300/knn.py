@@ -38,7 +38,8 @@ class Opts(C.Structure):
     _fields_ = [("h", C.c_int32), ("bound", C.c_int32), ("c_alpha", C.c_double), ("B0", C.c_int32),
                 ("B", C.c_int32), ("grow", C.c_int32), ("qid_base", C.c_uint64), ("mask_p", C.c_uint64),
                 ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32), ("block", C.c_int32),
-                ("metric", C.c_int32), ("sampling", C.c_int32), ("r0_tensor", C.c_int32)]
+                ("metric", C.c_int32), ("sampling", C.c_int32), ("r0_tensor", C.c_int32),
+                ("query_order", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -126,13 +127,14 @@ METRICS = {"l2": 0, "l1": 1}
 
 def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid_base=0, share_points=False,
               share_queries=False, max_ctas=0, threads=0, block=1, metric="l2", replace=True,
-              r0_tensor=False) -> Opts:
+              r0_tensor=False, query_order=True) -> Opts:
     """knn_opts for a call; `block` = coordinates per sample (1: single
     coordinates; g > 1: blocks of g consecutive coordinates, B0 and B then
     count blocks); `metric` = "l2" (squared l2, the paper's) or "l1";
     `replace` = False draws each pair's coordinates without replacement;
     `r0_tensor` = True forms round 0 under shared coordinates as a
-    tensor-core contraction (knn_opts.r0_tensor)."""
+    tensor-core contraction (knn_opts.r0_tensor); `query_order` = False
+    keeps the batch order of dataset calls (knn_opts.query_order)."""
     o = Opts()
     lib().knn_opts_default(C.byref(o))
     o.h = -1 if h is None else int(h)
@@ -148,6 +150,7 @@ def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid
     o.metric = METRICS[metric] if isinstance(metric, str) else int(metric)
     o.sampling = 0 if replace else 1
     o.r0_tensor = 1 if r0_tensor else 0
+    o.query_order = 1 if query_order else 0
     return o
 
 

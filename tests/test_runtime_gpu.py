@@ -80,3 +80,23 @@ def test_autotune_over_sampling_units(data, tmp_path):
     ri, rd = knn.rerank(ds.X, H, res["idx"], 10)
     ti, td = ds.exact(H, 10, screen="f32")
     assert runtime.recall(ri, rd, ti, td) >= 0.999
+
+
+@pytest.mark.parametrize("share", [False, True])
+def test_query_locality_order_changes_only_the_schedule(share):
+    """Dataset calls take a batch's queries in a locality order (SimHash of
+    the query); every output, the decision log included, equals the batch
+    order's bit for bit."""
+    X, Q = synth.pixel_mixture(30000, 160, 300, seed=17)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    opt = dict(bound="exp", c_alpha=1e-3, B0=16, B=16, grow=1, threads=512)
+    if share:
+        opt.update(share_points=True, share_queries=True)
+    with knn.Dataset(Xd, copies=("bf16",)) as ds:
+        if share:
+            ds.share(3, copies=("bf16",))
+        a = ds.adaptive(Qd, 10, 0.01, 3, storage="bf16", trace=True, query_order=True, **opt)
+        b = ds.adaptive(Qd, 10, 0.01, 3, storage="bf16", trace=True, query_order=False, **opt)
+        torch.cuda.synchronize()
+    for key in a:
+        assert torch.equal(a[key], b[key]), key

@@ -100,7 +100,9 @@ def test_each_request_same_alone_and_in_the_mix(two_datasets):
         alone[r.rid] = rr
         assert rr.batch_size == r.Q.shape[0]
     s = serve.Server(dss, cfg, slots=3, max_batch=96)
-    arrivals = [(0.0005 * i, _clone(r)) for i, r in enumerate(reqs)]
+    # all arrive at once: three take the slots, the rest wait and are packed
+    # into shared launches as slots free up (independent of kernel speed)
+    arrivals = [(0.0, _clone(r)) for r in reqs]
     done = s.run(arrivals)
     assert len(done) == len(reqs)
     assert any(r.batch_size > r.Q.shape[0] for r in done)       # requests really were batched together
