@@ -833,7 +833,7 @@ def run_serve(args):
     for i, (n, m) in enumerate(SERVE["datasets"]):
         n = max(4096, int(n * scale))
         X, P = synth.mixture_planted(n, m, SERVE["pool"], seed=100 + i)
-        ds = knn.Dataset(torch.from_numpy(X).cuda(), copies=("bf16", "screen"))
+        ds = knn.Dataset(torch.from_numpy(X).cuda(), copies=("bf16", "screen_f16"))
         extra = {}
         if args.serve_shared:
             ds.share(0, copies=("bf16",))
@@ -926,9 +926,9 @@ def run_sweep(args):
         ("blocks_f32_g8", "f32", {"block": 8}, ((2, 2, 1), (4, 4, 1), (8, 8, 1))),
         ("blocks_bf16_g16", "bf16", {"block": 16}, ((2, 2, 1), (4, 4, 1), (8, 8, 1))),
         ("blocks_fp8_g32", "fp8", {"block": 32}, ((2, 2, 1), (4, 4, 1))),
-        ("shared_f32", "f32", {"share_points": True, "share_queries": True},
+        ("shared_f32", "f32", {"share_points": True, "share_queries": True, "r0_tensor": True},
          ((8, 8, 1), (16, 16, 1), (32, 32, 1), (64, 64, 1))),
-        ("shared_bf16", "bf16", {"share_points": True, "share_queries": True},
+        ("shared_bf16", "bf16", {"share_points": True, "share_queries": True, "r0_tensor": True},
          ((8, 8, 1), (16, 16, 1), (32, 32, 1), (64, 64, 1))),
     ]
     if args.sweep_variants:
@@ -940,7 +940,7 @@ def run_sweep(args):
         Xd = torch.from_numpy(X).to(dev)
         Qd = torch.from_numpy(Qall[:nq]).to(dev)
         Hd = torch.from_numpy(Qall[nq:]).to(dev)
-        ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen"))
+        ds = knn.Dataset(Xd, copies=("bf16", "fp8", "screen_f16"))
         ds.share(0, copies=("f32", "bf16"))
         ti, td = ds.exact(Qd, k, screen="f32")
         tin, tdn = ti.cpu().numpy(), td.cpu().numpy()
@@ -957,7 +957,7 @@ def run_sweep(args):
             return e0.elapsed_time(e1) / steps, out
 
         row = {"gap": gap}
-        ex_ms, (ei, _) = timed(lambda: ds.exact(Qd, k, screen="bf16x3"))
+        ex_ms, (ei, _) = timed(lambda: ds.exact(Qd, k, screen="f16"))
         row["exact_tc"] = {"queries_per_s": round(nq / (ex_ms / 1e3), 1), "ms": round(ex_ms, 3),
                            "agrees": bool(torch.equal(ei, ti))}
         sm_ms, _ = timed(lambda: ds.exact(Qd, k, screen="f32"), steps=1)

@@ -282,13 +282,24 @@ class Dataset:
         _check(rc)
         return out
 
-    def exact_workspace_size(self, nq: int, screen: str = "bf16x3") -> int:
+    def best_screen(self) -> str:
+        """The fastest screen whose operand the dataset holds: FP16, then
+        BF16x3, then single BF16, else the FP32 SIMT screen."""
+        for copy, screen in (("screen_f16", "f16"), ("screen", "bf16x3"), ("screen_bf16", "bf16")):
+            if copy in self.copies:
+                return screen
+        return "f32"
+
+    def exact_workspace_size(self, nq: int, screen: str | None = None) -> int:
+        screen = screen or self.best_screen()
         return int(lib().knn_exact_ds_workspace_size(self._h, SCREENS[screen], int(nq)))
 
-    def exact(self, Q: torch.Tensor, k: int, screen: str = "bf16x3", workspace: torch.Tensor | None = None,
+    def exact(self, Q: torch.Tensor, k: int, screen: str | None = None, workspace: torch.Tensor | None = None,
               stream=None):
-        """knn_exact_ds: the naive exact method with the chosen screen.
+        """knn_exact_ds: the naive exact method with the chosen screen (by
+        default the fastest one the dataset holds, best_screen()).
         Returns (idx [nq,k] int64, dist [nq,k] f64)."""
+        screen = screen or self.best_screen()
         nq = Q.shape[0]
         idx = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
         dist = torch.empty((nq, k), dtype=torch.float64, device=Q.device)
