@@ -64,12 +64,12 @@ RECALL_TARGET = 0.999
 # time from the library's CUDA events. A record is reported only while the
 # kernel sources hash to the recorded value and the launch configuration
 # matches; otherwise the roofline's traffic is null.
-TRAFFIC_CAPTURE = {"sha1": "8ff44444fd7f8003f6fbf6377eec7dfbcc6db792",
+TRAFFIC_CAPTURE = {"sha1": "72bd7ffcc9078d6d6dff791d2ed6f37faf6150f4",
                    "records": [
                        {"config": {"c_alpha": 1e-3, "B0": 8, "B": 8, "grow": 1, "threads": 1024, "nq": 1024},
-                        "rounds_bytes": 21.589e9 + 1.169e9, "rounds_ms": 4.95},
+                        "rounds_bytes": 14.037e9 + 1.097e9, "rounds_ms": 4.46},
                        {"config": {"c_alpha": 3e-4, "B0": 16, "B": 16, "grow": 1, "threads": 1024, "nq": 1024},
-                        "rounds_bytes": 11.956e9 + 0.450e9, "rounds_ms": 3.22},
+                        "rounds_bytes": 4.686e9 + 0.336e9, "rounds_ms": 2.72},
                    ]}
 # Schedule of the oracle runs when no GPU line gives one (the autotuner's
 # usual choice on this workload).
