@@ -1061,7 +1061,7 @@ def run_profile_step(args):
     dflt = lambda v, d: d if v is None else v
     opts = dict(bound="exp", c_alpha=args.c_alpha or 1e-3, B0=dflt(args.B0, 16), B=dflt(args.B, 16),
                 grow=dflt(args.grow, 1), threads=args.threads,
-                block=args.block)
+                block=args.block, row_pass=not args.no_row_pass)
     if args.share:
         ds.share(0, copies=(args.storage,))
         opts.update(share_points=True, share_queries=True, r0_tensor=args.r0_tensor)
@@ -1081,6 +1081,16 @@ def run_profile_step(args):
            "ms_per_step": round(e0.elapsed_time(e1) / args.steps, 4), "evals": int(res["evals"].sum().item())}
     if args.phases:
         out.update(phase_report(knn.phase_clocks(), opts, args, w))
+    else:
+        # the library's own CUDA events around its kernels, over 3 eager calls
+        knn.kernel_timing(True)
+        knn.kernel_times(reset=True)
+        for _ in range(3):
+            ds.adaptive(Qd, w["k"], w["delta"], 0, storage=args.storage, **opts)
+        torch.cuda.synchronize()
+        r0_ms, loop_ms = knn.kernel_times(reset=True)
+        knn.kernel_timing(False)
+        out.update(round0_ms=round(r0_ms / 3, 4), rounds_ms=round(loop_ms / 3, 4))
     print(json.dumps(out), flush=True)
 
 
@@ -1166,6 +1176,8 @@ def main():
     ap.add_argument("--block", type=int, default=1)
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"])
     ap.add_argument("--share", action="store_true", help="shared coordinates (both counter masks zero)")
+    ap.add_argument("--no-row-pass", dest="no_row_pass", action="store_true",
+                    help="--profile-step: every round gathers its own draws (knn_opts.row_pass = 0)")
     ap.add_argument("--phases", action="store_true",
                     help="with --profile-step: phase-timing build, per-phase shares of the round loop")
     ap.add_argument("--sweep-gaps", dest="sweep_gaps", default=None, help="comma-separated gap ratios")

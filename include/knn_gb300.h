@@ -116,6 +116,16 @@ typedef struct {
                           * batch mean), so queries near one another run at the same time and the rows
                           * they keep active stay in L2; 0: batch order. Only the schedule changes: a
                           * query's draws, decisions and result depend on its id, not its turn. */
+    int32_t row_pass;   /* 1 (default): per-pair draws over the FP32 data (storage KNN_STORE_F32, single
+                         * coordinates, with replacement) take row passes: from a round r >= 2 whose
+                         * active points nearly all survived the round before (at least 3/4 of them), or
+                         * from a round drawing at least m/8 coordinates per point, and with at most
+                         * 8192 points active, a warp reads each active point's row once and forms the
+                         * sums of that round and of up to 5 later ones (up to the exact distance) from
+                         * it, each in the order that round's own gather uses; the later rounds read
+                         * their sums back. Results are the same bit for bit; draws of rounds a point
+                         * no longer reaches are computed and dropped (not counted in out_evals).
+                         * 0: every round gathers its own draws. */
 } knn_opts;
 
 void knn_opts_default(knn_opts* opts);

@@ -27,6 +27,7 @@ extern "C" void knn_opts_default(knn_opts* o) {
   o->sampling = KNN_SAMPLE_WITH;
   o->r0_tensor = 0;
   o->query_order = 1;
+  o->row_pass = 1;
 }
 
 extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, int32_t k, const knn_opts* opts) {
@@ -137,6 +138,7 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.B = o.B;
   a.grow = o.grow;
   a.seed = seed;
+  a.rk = philox_keys(seed);
   a.qid_base = o.qid_base;
   a.mask_p = o.mask_p;
   a.mask_q = o.mask_q;
@@ -149,6 +151,8 @@ extern "C" knn_status knn_adaptive(const float* X, int64_t n, int32_t m, const f
   a.ws_acc_U = c.acc_U;
   a.ws_acc_L = c.acc_L;
   a.acc_cap = p.acc_cap;
+  a.ws_F = c.F;
+  a.fuse_cap = p.fuse_cap;
   a.queue = c.queue;
   a.out_idx = out_idx;
   a.out_count = out_count;
@@ -286,6 +290,7 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.B = o.B;
   a.grow = o.grow;
   a.seed = seed;
+  a.rk = philox_keys(seed);
   a.qid_base = o.qid_base;
   a.mask_p = o.mask_p;
   a.mask_q = o.mask_q;
@@ -298,6 +303,8 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   a.ws_acc_U = c.acc_U;
   a.ws_acc_L = c.acc_L;
   a.acc_cap = p.acc_cap;
+  a.ws_F = c.F;
+  a.fuse_cap = p.fuse_cap;
   a.queue = c.queue;
   a.out_idx = out_idx;
   a.out_count = out_count;

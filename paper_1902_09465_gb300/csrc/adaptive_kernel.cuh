@@ -65,6 +65,7 @@ struct AdaptiveArgs {
   float a_c0, a_c1, c_alpha;  // host-precomputed constants of alpha(u)
   int32_t B0, B, grow;
   uint64_t seed, qid_base, mask_p, mask_q;
+  PhiloxKeys rk;        // round keys of seed (philox_keys)
   const uint32_t* xrange;  // ordered keys of min(X), max(X) over finite values; [2] non-finite flag
   int32_t* ws_ids;
   float* ws_S;
@@ -97,7 +98,19 @@ struct AdaptiveArgs {
   const int32_t* qorder = nullptr;  // order in which CTAs take the queries (null: batch order)
   int32_t r0_resum = 0; // the round-0 sums came from the tensor-core contraction: the points the
                         // round-0 filter keeps get their sums again, sample by sample
+  float* ws_F = nullptr;  // row passes: later rounds' sums per active slot, [2][kFuseRounds][fuse_cap] per CTA
+  int32_t fuse_cap = 0;   // slots a row pass may cover (0: no row passes)
 };
+
+// Row passes (per-pair draws over the FP32 data): once the active points
+// mostly survive from one round to the next, or a round draws at least m/8
+// coordinates per point, a warp reads each active point's row once into
+// shared memory and takes the sums of up to kFuseRounds rounds from it (the
+// remaining ones up to the exact distance when they fit), each in the order
+// its own round's gather would use. Later rounds read their sums back.
+constexpr int kFuseRounds = 6;
+constexpr int kFuseParts = kFuseRounds * 32;  // per-warp partial sums (virtual lanes of every round)
+constexpr int kFuseCap = 8192;
 
 // Phase timing (compiled in only with KNN_PHASE_TIMING): thread 0 of each CTA
 // adds the SM clocks spent since the previous boundary to phase i of
@@ -179,6 +192,11 @@ struct AdaptiveShared {
   int nacc_add;
   int bad;
   float tauU, tauL;
+  // the rounds of a row pass: samples [f_T[i], f_Tn[i]); the last one exact
+  // if f_exact; sampled round i has virtual lanes f_uoff[i] .. f_uoff[i+1]-1
+  int f_nr, f_exact;
+  int f_T[kFuseRounds], f_Tn[kFuseRounds], f_uoff[kFuseRounds + 1];
+  int4 f_unit[kFuseParts];  // virtual lane u: (T, Tn, G, v) of its round
 };
 
 // Shared coordinates (both counter masks zero): every pair draws the same
@@ -412,7 +430,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
   bool has;
   item(0, sidx, id, b, has);
   // (without replacement one item per pair: the last two blocks of its stream, the round keys)
-  Draws8 ph = has ? pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.seed)
+  Draws8 ph = has ? pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.rk)
                   : Draws8{};
   float part = 0.0f;
   for (int t = 0; t < nitems; ++t) {
@@ -438,7 +456,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
     // the next item's Philox while the loads are in flight
     if (t + 1 < nitems) {
       item(t + 1, sidx, id, b, has);
-      if (has) ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.seed);
+      if (has) ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.rk);
     }
     // consume
     if (cur_has) {
@@ -542,7 +560,7 @@ __device__ __forceinline__ void gather_blocks(const AdaptiveArgs& a, uint64_t qi
     const uint64_t b = blo + (uint64_t)(gl + jt * G);
     if (sidx < nact && b <= bhi) {
       const int id = (r == 0) ? sidx : idc[sidx];
-      const Draws8 ph = pair_draws8((uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.seed);
+      const Draws8 ph = pair_draws8((uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.rk);
       const Tp* xr = G0 + (size_t)id * (size_t)m;
       const float sc = E::kScaled ? __ldg(a.gscale + id) : 1.0f;
       const int64_t s0 = (int64_t)(b << 3);
@@ -658,6 +676,124 @@ __device__ __forceinline__ void gather_exact(const AdaptiveArgs& a, int r, int n
   }
 }
 
+// Row pass (per-pair draws over the FP32 data): a warp takes one active
+// point at a time, reads its row once (its differences to the query go to
+// shared memory) and forms the sums of the pass's rounds from it. A sampled round's sum is that of
+// gather_sampled: virtual lane v of the round's G sums its blocks v, v + G,
+// ... in turn (8 draws each, in draw order) and the G partial sums go through
+// the same butterfly; an exact round's sum is that of gather_exact (lane
+// order of its loads, then the full butterfly). The first round updates the
+// running sums like a gather; round i > 0 goes to F[(i-1) cap + slot].
+template <int NT, bool L1>
+__device__ __forceinline__ void gather_fused(const AdaptiveArgs& a, const AdaptiveShared<NT>& sh, uint64_t qid, int nact,
+                                          const float* qs, const int32_t* idc, float* Sc, float* Cc,
+                                          uint32_t* hist, float* rows, float* F) {
+  const int m = a.m;
+  const int mpad = (m + 3) & ~3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* row = rows + (size_t)warp * (size_t)(mpad + kFuseParts);
+  float* P = row + mpad;
+  const int nr = sh.f_nr;
+  const int nsamp = sh.f_exact ? nr - 1 : nr;  // sampled rounds
+  const int nunits = sh.f_uoff[nsamp];
+  const uint64_t qfield = qid & a.mask_q;
+  const int cap = a.fuse_cap;
+  for (int s = warp; s < nact; s += NT / 32) {
+    // the row's differences to the query, x_j - q_j (each draw then takes one
+    // shared-memory read; the same FP32 subtraction every gather performs)
+    const int id = idc[s];
+    const float* xr = a.X + (size_t)id * (size_t)m;
+    if (a.vec) {
+      for (int j4 = lane; j4 < (m >> 2); j4 += 32) {
+        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr) + j4);
+        const float4 q4 = reinterpret_cast<const float4*>(qs)[j4];
+        reinterpret_cast<float4*>(row)[j4] = make_float4(x4.x - q4.x, x4.y - q4.y, x4.z - q4.z, x4.w - q4.w);
+      }
+    } else {
+      for (int j = lane; j < m; j += 32) row[j] = __ldg(xr + j) - qs[j];
+    }
+    __syncwarp();
+    const uint64_t pfield = (uint64_t)id & a.mask_p;
+    for (int u = lane; u < nunits; u += 32) {
+      const int4 ud = sh.f_unit[u];
+      const int T = ud.x, Tn = ud.y, G = ud.z, v = ud.w;
+      const int bhi = (Tn - 1) >> 3;
+      float part = 0.0f;
+      for (int b = (T >> 3) + v; b <= bhi; b += G) {
+        const Draws8 ph = pair_draws8((uint32_t)b, pfield, qfield, a.rk);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const int sv = 8 * b + w;
+          if (sv >= T && sv < Tn) {
+            const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+            part = add_term<L1>(row[j], part);
+          }
+        }
+      }
+      P[u] = part;
+    }
+    __syncwarp();
+    for (int i = 0; i < nr; ++i) {
+      float x = 0.0f;
+      if (i == nsamp) {  // the exact round
+        if (a.vec) {
+          for (int j = lane * 4; j < m; j += 128) {
+            const float4 d4 = *reinterpret_cast<const float4*>(row + j);
+            x = add_term<L1>(d4.x, x);
+            x = add_term<L1>(d4.y, x);
+            x = add_term<L1>(d4.z, x);
+            x = add_term<L1>(d4.w, x);
+          }
+        } else {
+          for (int j = lane; j < m; j += 32) x = add_term<L1>(row[j], x);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      } else {
+        const int G = sh.f_uoff[i + 1] - sh.f_uoff[i];
+        if (lane < G) x = P[sh.f_uoff[i] + lane];
+#pragma unroll
+        for (int o = 16; o; o >>= 1)
+          if (o < G) x += __shfl_xor_sync(0xffffffffu, x, o);
+      }
+      if (lane == 0) {
+        if (i == 0) {  // this round: Kahan-compensated running sum, as a gather updates it
+          const float S0 = Sc[s], c0 = Cc[s];
+          const float y = x - c0;
+          const float tt = S0 + y;
+          Cc[s] = (tt - S0) - y;
+          Sc[s] = tt;
+          atomicAdd(&hist[f2key(tt) >> 20], 1u);
+        } else {
+          F[(size_t)(i - 1) * (size_t)cap + s] = x;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// A round whose sums a row pass formed: the running sums take them as a
+// gather would (exact rounds replace them).
+template <int NT>
+__device__ __forceinline__ void gather_from_pass(int nact, bool exact, const float* Fc, float* Sc, float* Cc,
+                                                 uint32_t* hist) {
+  for (int s = threadIdx.x; s < nact; s += NT) {
+    const float x = Fc[s];
+    float S;
+    if (exact) {
+      S = x;
+    } else {
+      const float S0 = Sc[s], c0 = Cc[s];
+      const float y = x - c0;
+      S = S0 + y;
+      Cc[s] = (S - S0) - y;
+    }
+    Sc[s] = S;
+    atomicAdd(&hist[f2key(S) >> 20], 1u);
+  }
+}
+
 // Round 0 from the point-major pass, with tile minima. tau_U' = (k-th
 // smallest tile minimum)/T + w is at least tau_U (the k smallest tile minima
 // are sums of k distinct points), so a point whose LCB exceeds tau_U' is
@@ -756,6 +892,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   float* actL = actU + (kMaxKH + 4);
   int32_t* oid = reinterpret_cast<int32_t*>(actL + (kMaxKH + 4));
   float* qsp = reinterpret_cast<float*>(oid + kMaxKH);  // permuted query (shared coordinates only)
+  float* frows = qsp + (E::kPerm ? ((m + 7) & ~7) : 0);  // row passes: a row and partials per warp
+  constexpr bool kRowPass = std::is_same<E, ElemF32>::value;
   float* tmpS = actU;                              // reused in the output phase
   int32_t* tmpI = reinterpret_cast<int32_t*>(actL);
 
@@ -770,6 +908,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   float* acc_d = a.ws_acc_d + slot * (size_t)a.acc_cap;
   float* acc_U = a.ws_acc_U + slot * (size_t)a.acc_cap;
   float* acc_L = a.ws_acc_L + slot * (size_t)a.acc_cap;
+  // row passes: sums of later rounds per active slot, ping-pong like the slots
+  float* const F0 = a.ws_F ? a.ws_F + slot * 2 * kFuseRounds * (size_t)a.fuse_cap : nullptr;
+  auto Fcol = [&](int b, int c) { return F0 + ((size_t)b * kFuseRounds + c) * (size_t)a.fuse_cap; };
   KNN_PHASE_START;
 
   for (;;) {
@@ -849,6 +990,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     }
 
     int nact = (int)n, nacc = 0, cur = 0, r = 0, term = 0;
+    int fcols = 0, nact_prev = 0;  // rounds held in F; active points at the previous round's start
     int64_t T = 0, evals = 0;
     float min_elim = INFINITY;
     for (;;) {
@@ -879,9 +1021,51 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         for (int64_t i = tid; i < n; i += NT) mx = fmaxf(mx, R0q[i]);
         copy_width(block_max<NT>(mx, sh.bs));
       }
+      // a row pass from this round: after a round that kept at least 3/4 of its
+      // points, or for a round drawing m/8 coordinates or more per point
+      bool fuse_now = false;
+      if constexpr (kRowPass) {
+        fuse_now = a.fuse_cap > 0 && fcols == 0 && r >= 1 && !exact && nact <= a.fuse_cap && a.G == a.X &&
+                   ((r >= 2 && 4 * (int64_t)nact >= 3 * (int64_t)nact_prev) || 8 * Br >= m);
+        if (fuse_now && tid == 0) {
+          int64_t Ti = T;
+          int nr = 0, u = 0, ex = 0;
+          sh.f_uoff[0] = 0;
+          while (nr < kFuseRounds) {
+            const int64_t Bi = a.grow ? (Ti > a.B ? Ti : (int64_t)a.B) : (int64_t)a.B;
+            const bool xi = Ti + Bi >= a.Mb;
+            const int64_t Tni = xi ? a.Mb : Ti + Bi;
+            sh.f_T[nr] = (int)Ti;
+            sh.f_Tn[nr] = (int)Tni;
+            if (!xi) {
+              const int nb = (int)(((Tni - 1) >> 3) - (Ti >> 3) + 1);
+              int G = 1;
+              while (G < nb && G < 32) G <<= 1;
+              for (int v = 0; v < G; ++v) sh.f_unit[u + v] = make_int4((int)Ti, (int)Tni, G, v);
+              u += G;
+            }
+            sh.f_uoff[++nr] = u;
+            Ti = Tni;
+            if (xi) {
+              ex = 1;
+              break;
+            }
+          }
+          sh.f_nr = nr;
+          sh.f_exact = ex;
+        }
+      }
       for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
       __syncthreads();
       KNN_PHASE(0);  // setup
+      // slots' sums of later rounds to carry through this round's compaction
+      int fsrc = 0, fmove = 0;
+      if (fuse_now) {
+        fmove = sh.f_nr - 1;
+      } else if (fcols > 0) {
+        fsrc = 1;
+        fmove = fcols - 1;
+      }
       if (flt) {
         nact = round0_filter<NT>(a, q, n, k, w, Tf, hist, buf, sh, ids0 + (size_t)cur * n, Sc,
                                  ids0 + (size_t)(cur ^ 1) * n, S0 + (size_t)(cur ^ 1) * n, lcode, lS, &min_elim);
@@ -895,6 +1079,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
           }
         }
       }
+      else if (fcols > 0)  // a row pass formed this round's sums
+        gather_from_pass<NT>(nact, exact, Fcol(cur, 0), Sc, Cc, hist);
+      else if (fuse_now)
+        gather_fused<NT, L1>(a, sh, qid, nact, qs, idc, Sc, Cc, hist, frows, Fcol(cur, 0));
       else if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT, L1>(a, r, nact, qs, idc, Sc, hist);
       else if (pre)
@@ -989,6 +1177,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
             idn[pos] = myid[e];
             Sn[pos] = myS[e];
             Cn[pos] = myC[e];
+            for (int c = 0; c < fmove; ++c) Fcol(cur ^ 1, c)[pos] = Fcol(cur, fsrc + c)[cb + tid * kIPT + e];
             ++pos;
           }
         }
@@ -997,7 +1186,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       rmin = block_min<NT>(rmin, sh.bs);  // also orders sh.nacc_add
       KNN_PHASE(5);  // decide + compact
       nacc = min(nacc + sh.nacc_add, a.acc_cap);
+      nact_prev = nact;
       nact = out_base;
+      fcols = fmove;
       min_elim = fminf(min_elim, rmin);
       T = Tn;
       cur ^= 1;
@@ -1242,7 +1433,7 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
       float part = 0.0f;
       if (pi < np && gl < nblk) {
         const uint64_t id = (uint64_t)(p0 + pi);
-        const Draws8 ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)gl, id & a.mask_p, qfield, a.seed);
+        const Draws8 ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)gl, id & a.mask_p, qfield, a.rk);
         const float* xr = rows + (size_t)pi * m;
         if constexpr (!E::kBlk) {
 #pragma unroll
@@ -1446,11 +1637,14 @@ static __global__ void minmax_kernel(const float* __restrict__ X, size_t count, 
 
 constexpr int kAdaptiveNT = 512;  // default threads per CTA (256 is the other choice)
 
-static size_t adaptive_smem_bytes(int m, bool perm = false) {
+// Dynamic shared memory of the round loop: query row, histogram, select
+// buffer, accepted lists, the permuted query (shared coordinates) and, with
+// row passes, one row and kFuseParts partial sums per warp.
+static size_t adaptive_smem_bytes(int m, bool perm = false, int fuse_threads = 0) {
   const size_t mpad = (size_t)((m + 3) & ~3);
   const size_t mp = (size_t)((m + 7) & ~7);
   return mpad * 4 + (size_t)kHistBins * 4 + (size_t)kSelCap * 4 + 2 * (size_t)(kMaxKH + 4) * 4 +
-         (size_t)kMaxKH * 4 + (perm ? mp * 4 : 0);
+         (size_t)kMaxKH * 4 + (perm ? mp * 4 : 0) + (size_t)(fuse_threads / 32) * (mpad + kFuseParts) * 4;
 }
 
 struct AdaptivePlan {
@@ -1458,6 +1652,7 @@ struct AdaptivePlan {
   int threads = kAdaptiveNT;
   int acc_cap = 0;
   size_t smem = 0;
+  int fuse_cap = 0;  // slots a row pass may cover (0: none)
 };
 
 // The round-loop kernel instantiated for a thread count (256, 512 or 1024;
@@ -1481,6 +1676,14 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   if (s != KNN_OK) return s;
   p->threads = (o && (o->threads == 256 || o->threads == 1024)) ? o->threads : kAdaptiveNT;
   p->smem = adaptive_smem_bytes(m, E::kPerm);
+  p->fuse_cap = 0;
+  if (std::is_same<E, ElemF32>::value && o && o->row_pass) {  // row passes: per-pair draws of the FP32 data
+    const size_t f = adaptive_smem_bytes(m, false, p->threads);
+    if (f + 1024 <= di.smem_optin) {
+      p->smem = f;
+      p->fuse_cap = (int)std::min<int64_t>(n, kFuseCap);
+    }
+  }
   const void* fn = rounds_kernel_for<E>(p->threads, o && o->metric == KNN_METRIC_L1);
   s = cuda_check(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem),
                  "cudaFuncSetAttribute(adaptive)");
@@ -1499,7 +1702,6 @@ static knn_status plan_adaptive(int64_t n, int32_t m, int32_t nq, int32_t k, con
   if (grid < 1) grid = 1;
   p->grid = grid;
   p->acc_cap = 2 * k + 2;
-  (void)n;
   return KNN_OK;
 }
 
@@ -1515,6 +1717,13 @@ static void launch_rounds_metric(const AdaptivePlan& p, const AdaptiveArgs& a, c
 
 template <class E>
 static knn_status launch_rounds(const AdaptivePlan& p, const AdaptiveArgs& a, cudaStream_t stream) {
+  // the plan may come from another element type of the same layout (draws
+  // without replacement share the per-pair plan): the launched kernel gets its
+  // own shared-memory limit
+  const knn_status s = cuda_check(cudaFuncSetAttribute(rounds_kernel_for<E>(p.threads, a.l1),
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
+                                  "cudaFuncSetAttribute(adaptive)");
+  if (s != KNN_OK) return s;
   if (a.l1)
     launch_rounds_metric<E, true>(p, a, stream);
   else
@@ -1532,6 +1741,7 @@ struct AdaptiveCarve {
   float* acc_d;
   float* acc_U;
   float* acc_L;
+  float* F;
 };
 
 static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, AdaptiveCarve* out) {
@@ -1547,6 +1757,7 @@ static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, Adapti
   c.acc_d = cv.take<float>(acc);
   c.acc_U = cv.take<float>(acc);
   c.acc_L = cv.take<float>(acc);
+  c.F = p.fuse_cap ? cv.take<float>((size_t)p.grid * 2 * kFuseRounds * (size_t)p.fuse_cap) : nullptr;
   if (out) *out = c;
   return cv.off;
 }

@@ -98,6 +98,7 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   a.B = o.B;
   a.grow = o.grow;
   a.seed = seed;
+  a.rk = philox_keys(seed);
   a.qid_base = o.qid_base;
   a.mask_p = o.mask_p;
   a.mask_q = o.mask_q;
@@ -110,6 +111,8 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   a.ws_acc_U = c.acc_U;
   a.ws_acc_L = c.acc_L;
   a.acc_cap = p.acc_cap;
+  a.ws_F = c.F;
+  a.fuse_cap = p.fuse_cap;
   a.queue = c.queue;
   a.out_idx = out_idx;
   a.out_count = out_count;

@@ -64,6 +64,59 @@ __device__ __forceinline__ Draws8 pair_draws8(uint32_t item, uint64_t point_fiel
   return d;
 }
 
+// The ten round keys of a seed, (k0 + r W0, k1 + r W1) for r = 0 .. 9, held
+// in a kernel's parameters: the rounds then read them as constant operands
+// instead of adding the Weyl increments per call.
+struct PhiloxKeys {
+  uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k[2 * r] = k0;
+    K.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+
+// philox4x32_10 with the round keys given
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                  const PhiloxKeys& K) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+    const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+    c0 = hi1 ^ c1 ^ K.k[2 * r];
+    c1 = lo1;
+    c2 = hi0 ^ c3 ^ K.k[2 * r + 1];
+    c3 = lo0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// pair_draws8 with the seed's round keys given
+__device__ __forceinline__ Draws8 pair_draws8(uint32_t item, uint64_t point_field, uint64_t query_field,
+                                              const PhiloxKeys& K) {
+  const uint32_t p = (uint32_t)point_field, ql = (uint32_t)query_field, qh = (uint32_t)(query_field >> 32);
+  const uint4 a = philox4x32_10_rk(2u * item, p, ql, qh, K);
+  const uint4 b = philox4x32_10_rk(2u * item + 1u, p, ql, qh, K);
+  Draws8 d;
+  d.w[0] = a.x;
+  d.w[1] = a.y;
+  d.w[2] = a.z;
+  d.w[3] = a.w;
+  d.w[4] = b.x;
+  d.w[5] = b.y;
+  d.w[6] = b.z;
+  d.w[7] = b.w;
+  return d;
+}
+
 // Item whose two blocks are the last of a pair's stream (blocks 2^32 - 2 and
 // 2^32 - 1): the round keys of the draws without replacement.
 constexpr uint32_t kWorKeyItem = 0x7FFFFFFFu;

@@ -39,7 +39,7 @@ class Opts(C.Structure):
                 ("B", C.c_int32), ("grow", C.c_int32), ("qid_base", C.c_uint64), ("mask_p", C.c_uint64),
                 ("mask_q", C.c_uint64), ("threads", C.c_int32), ("max_ctas", C.c_int32), ("block", C.c_int32),
                 ("metric", C.c_int32), ("sampling", C.c_int32), ("r0_tensor", C.c_int32),
-                ("query_order", C.c_int32)]
+                ("query_order", C.c_int32), ("row_pass", C.c_int32)]
 
 
 _P = C.c_void_p
@@ -127,14 +127,16 @@ METRICS = {"l2": 0, "l1": 1}
 
 def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid_base=0, share_points=False,
               share_queries=False, max_ctas=0, threads=0, block=1, metric="l2", replace=True,
-              r0_tensor=False, query_order=True) -> Opts:
+              r0_tensor=False, query_order=True, row_pass=True) -> Opts:
     """knn_opts for a call; `block` = coordinates per sample (1: single
     coordinates; g > 1: blocks of g consecutive coordinates, B0 and B then
     count blocks); `metric` = "l2" (squared l2, the paper's) or "l1";
     `replace` = False draws each pair's coordinates without replacement;
     `r0_tensor` = True forms round 0 under shared coordinates as a
     tensor-core contraction (knn_opts.r0_tensor); `query_order` = False
-    keeps the batch order of dataset calls (knn_opts.query_order)."""
+    keeps the batch order of dataset calls (knn_opts.query_order);
+    `row_pass` = False makes every round gather its own draws
+    (knn_opts.row_pass; the results are the same)."""
     o = Opts()
     lib().knn_opts_default(C.byref(o))
     o.h = -1 if h is None else int(h)
@@ -151,6 +153,7 @@ def make_opts(k, h=None, bound="footnote", c_alpha=1.0, B0=16, B=16, grow=0, qid
     o.sampling = 0 if replace else 1
     o.r0_tensor = 1 if r0_tensor else 0
     o.query_order = 1 if query_order else 0
+    o.row_pass = 1 if row_pass else 0
     return o
 
 
