@@ -428,6 +428,7 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
   int sidx, id;
   uint64_t b;
   bool has;
+  const int Ti = (int)T, Tni = (int)Tn;
   item(0, sidx, id, b, has);
   // (without replacement one item per pair: the last two blocks of its stream, the round keys)
   Draws8 ph = has ? pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.rk)
@@ -437,32 +438,54 @@ __device__ __forceinline__ void gather_sampled(const AdaptiveArgs& a, uint64_t q
     // issue the current item's loads
     float xv[8];
     int jj[8];
-    bool ok[8];
     const Tp* xr = G0 + (size_t)id * (size_t)m;
-    const int64_t s0 = (int64_t)(b << 3);
+    const int s0 = (int)(b << 3);  // sampled rounds have Tn < m
+    // draws of the item inside [T, Tn): bit w for draw s0 + w
+    uint32_t okm = 0;
+    if (has) {
+      if (s0 >= Ti && s0 + 8 <= Tni) {
+        okm = 0xFFu;
+      } else {
 #pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      const int64_t s = s0 + w;
-      ok[w] = has && (s >= T) && (s < Tn);
-      if constexpr (E::kWor)
-        jj[w] = ok[w] ? wor_coordinate(ph, (uint32_t)s, (uint32_t)m, a.wor_h) : 0;  // s < Tn < m
-      else
+        for (int w = 0; w < 8; ++w) okm |= (uint32_t)(s0 + w >= Ti && s0 + w < Tni) << w;
+      }
+    }
+    if (!E::kWor && okm == 0xFFu) {
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
         jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
-      xv[w] = ok[w] ? E::load(xr + jj[w]) : 0.0f;
+        xv[w] = E::load(xr + jj[w]);
+      }
+    } else {
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        const bool ok = (okm >> w) & 1u;
+        if constexpr (E::kWor)
+          jj[w] = ok ? wor_coordinate(ph, (uint32_t)(s0 + w), (uint32_t)m, a.wor_h) : 0;
+        else
+          jj[w] = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+        xv[w] = ok ? E::load(xr + jj[w]) : 0.0f;
+      }
     }
     const float sc = (E::kScaled && has) ? __ldg(a.gscale + id) : 1.0f;
     const int cur_sidx = sidx;
-    const bool cur_has = has;
+    const uint32_t cur_okm = okm;
     // the next item's Philox while the loads are in flight
     if (t + 1 < nitems) {
       item(t + 1, sidx, id, b, has);
       if (has) ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)b, (uint64_t)id & a.mask_p, qfield, a.rk);
     }
     // consume
-    if (cur_has) {
+    if (cur_okm == 0xFFu) {
 #pragma unroll
       for (int w = 0; w < 8; ++w) {
-        if (ok[w]) {
+        const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
+        part = add_term<L1>(d, part);
+      }
+    } else if (cur_okm) {
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        if ((cur_okm >> w) & 1u) {
           const float d = (E::kScaled ? __fmul_rn(xv[w], sc) : xv[w]) - qs[jj[w]];
           part = add_term<L1>(d, part);
         }
@@ -721,12 +744,14 @@ __device__ __forceinline__ void gather_fused(const AdaptiveArgs& a, const Adapti
       float part = 0.0f;
       for (int b = (T >> 3) + v; b <= bhi; b += G) {
         const Draws8 ph = pair_draws8((uint32_t)b, pfield, qfield, a.rk);
+        if (8 * b >= T && 8 * b + 8 <= Tn) {  // the whole block is in the round
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          const int sv = 8 * b + w;
-          if (sv >= T && sv < Tn) {
-            const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
-            part = add_term<L1>(row[j], part);
+          for (int w = 0; w < 8; ++w) part = add_term<L1>(row[__umulhi(philox_word(ph, w), (uint32_t)m)], part);
+        } else {
+#pragma unroll
+          for (int w = 0; w < 8; ++w) {
+            const int sv = 8 * b + w;
+            if (sv >= T && sv < Tn) part = add_term<L1>(row[__umulhi(philox_word(ph, w), (uint32_t)m)], part);
           }
         }
       }
@@ -1079,9 +1104,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
           }
         }
       }
-      else if (fcols > 0)  // a row pass formed this round's sums
+      else if (kRowPass && fcols > 0)  // a row pass formed this round's sums
         gather_from_pass<NT>(nact, exact, Fcol(cur, 0), Sc, Cc, hist);
-      else if (fuse_now)
+      else if (kRowPass && fuse_now)
         gather_fused<NT, L1>(a, sh, qid, nact, qs, idc, Sc, Cc, hist, frows, Fcol(cur, 0));
       else if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT, L1>(a, r, nact, qs, idc, Sc, hist);
@@ -1177,7 +1202,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
             idn[pos] = myid[e];
             Sn[pos] = myS[e];
             Cn[pos] = myC[e];
-            for (int c = 0; c < fmove; ++c) Fcol(cur ^ 1, c)[pos] = Fcol(cur, fsrc + c)[cb + tid * kIPT + e];
+            if constexpr (kRowPass)
+              for (int c = 0; c < fmove; ++c) Fcol(cur ^ 1, c)[pos] = Fcol(cur, fsrc + c)[cb + tid * kIPT + e];
             ++pos;
           }
         }
@@ -1436,13 +1462,21 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
         const Draws8 ph = pair_draws8(E::kWor ? kWorKeyItem : (uint32_t)gl, id & a.mask_p, qfield, a.rk);
         const float* xr = rows + (size_t)pi * m;
         if constexpr (!E::kBlk) {
+          if (!E::kWor && gl * 8 + 8 <= a.B0) {  // the whole block is in round 0
 #pragma unroll
-          for (int w = 0; w < 8; ++w) {
-            if (gl * 8 + w < a.B0) {  // B0 < m: the draw index is below m
-              const int j = E::kWor ? wor_coordinate(ph, (uint32_t)(gl * 8 + w), (uint32_t)m, a.wor_h)
-                                    : (int)__umulhi(philox_word(ph, w), (uint32_t)m);
-              const float d = xr[j] - __ldg(qr + j);
-              part = add_term<L1>(d, part);
+            for (int w = 0; w < 8; ++w) {
+              const int j = (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+              part = add_term<L1>(xr[j] - __ldg(qr + j), part);
+            }
+          } else {
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+              if (gl * 8 + w < a.B0) {  // B0 < m: the draw index is below m
+                const int j = E::kWor ? wor_coordinate(ph, (uint32_t)(gl * 8 + w), (uint32_t)m, a.wor_h)
+                                      : (int)__umulhi(philox_word(ph, w), (uint32_t)m);
+                const float d = xr[j] - __ldg(qr + j);
+                part = add_term<L1>(d, part);
+              }
             }
           }
         } else {  // block samples, in gather_blocks' order
