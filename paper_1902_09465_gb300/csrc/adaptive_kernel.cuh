@@ -728,12 +728,12 @@ __device__ __forceinline__ void gather_fused(const AdaptiveArgs& a, const Adapti
     const float* xr = a.X + (size_t)id * (size_t)m;
     if (a.vec) {
       for (int j4 = lane; j4 < (m >> 2); j4 += 32) {
-        const float4 x4 = __ldg(reinterpret_cast<const float4*>(xr) + j4);
+        const float4 x4 = ld_stream4(reinterpret_cast<const float4*>(xr) + j4);
         const float4 q4 = reinterpret_cast<const float4*>(qs)[j4];
         reinterpret_cast<float4*>(row)[j4] = make_float4(x4.x - q4.x, x4.y - q4.y, x4.z - q4.z, x4.w - q4.w);
       }
     } else {
-      for (int j = lane; j < m; j += 32) row[j] = __ldg(xr + j) - qs[j];
+      for (int j = lane; j < m; j += 32) row[j] = ld_stream(xr + j) - qs[j];
     }
     __syncwarp();
     const uint64_t pfield = (uint64_t)id & a.mask_p;
@@ -1436,10 +1436,22 @@ __global__ void __launch_bounds__(kR0Threads) round0_kernel(AdaptiveArgs a, int 
   const int64_t p0 = (int64_t)blockIdx.x * rows_per_cta;
   const int np = (int)((n - p0) < rows_per_cta ? (n - p0) : rows_per_cta);
   const Tp* G0 = static_cast<const Tp*>(a.G);
-  for (int e = threadIdx.x; e < np * m; e += kR0Threads) {
-    const int pi = e / m, j = e - pi * m;
-    const float x = E::load(G0 + (size_t)(p0 + pi) * m + j);
-    rows[e] = E::kScaled ? __fmul_rn(x, __ldg(a.gscale + p0 + pi)) : x;
+  if constexpr (std::is_same<Tp, float>::value && !E::kScaled) {
+    // the tile's rows are one contiguous run of the data, read once
+    const float* src = static_cast<const float*>(a.G) + (size_t)p0 * m;
+    const int cnt = np * m;
+    if (a.vec) {  // m % 4 == 0 and 16-byte aligned rows
+      for (int e = threadIdx.x; e < (cnt >> 2); e += kR0Threads)
+        reinterpret_cast<float4*>(rows)[e] = ld_stream4(reinterpret_cast<const float4*>(src) + e);
+    } else {
+      for (int e = threadIdx.x; e < cnt; e += kR0Threads) rows[e] = ld_stream(src + e);
+    }
+  } else {
+    for (int e = threadIdx.x; e < np * m; e += kR0Threads) {
+      const int pi = e / m, j = e - pi * m;
+      const float x = E::load(G0 + (size_t)(p0 + pi) * m + j);
+      rows[e] = E::kScaled ? __fmul_rn(x, __ldg(a.gscale + p0 + pi)) : x;
+    }
   }
   __syncthreads();
   const int nblk = (a.B0 + 7) >> 3;

@@ -123,6 +123,22 @@ constexpr uint32_t kWorKeyItem = 0x7FFFFFFFu;
 
 __device__ __forceinline__ uint32_t philox_word(const Draws8& d, int w) { return d.w[w]; }
 
+// ------------------------------------------------------- streaming loads
+// Read-only loads that do not allocate in L1: rows read once (staged in
+// shared memory) leave L1 to the data that is reused.
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 // ------------------------------------------------------------------- keys
 // Unsigned keys whose integer order is the float order (-0 < +0; NaN sorts
 // above +inf with the sign bit clear, below -inf with it set).
