@@ -721,10 +721,12 @@ __device__ __forceinline__ void gather_fused(const AdaptiveArgs& a, const Adapti
   const int nunits = sh.f_uoff[nsamp];
   const uint64_t qfield = qid & a.mask_q;
   const int cap = a.fuse_cap;
+  int id_next = warp < nact ? idc[warp] : 0;  // point ids one step ahead
   for (int s = warp; s < nact; s += NT / 32) {
     // the row's differences to the query, x_j - q_j (each draw then takes one
     // shared-memory read; the same FP32 subtraction every gather performs)
-    const int id = idc[s];
+    const int id = id_next;
+    if (s + NT / 32 < nact) id_next = idc[s + NT / 32];
     const float* xr = a.X + (size_t)id * (size_t)m;
     if (a.vec) {
       for (int j4 = lane; j4 < (m >> 2); j4 += 32) {
@@ -758,41 +760,57 @@ __device__ __forceinline__ void gather_fused(const AdaptiveArgs& a, const Adapti
       P[u] = part;
     }
     __syncwarp();
-    for (int i = 0; i < nr; ++i) {
-      float x = 0.0f;
-      if (i == nsamp) {  // the exact round
+    // every round's sum: lane v < G holds virtual lane v's partial of a sampled
+    // round, every lane its share of the exact round; the butterflies of all
+    // rounds run side by side (a round adds over offsets below its G only)
+    float x[kFuseRounds];
+    int Gr[kFuseRounds];
+#pragma unroll
+    for (int i = 0; i < kFuseRounds; ++i) {
+      x[i] = 0.0f;
+      Gr[i] = 0;
+      if (i < nsamp) {
+        Gr[i] = sh.f_uoff[i + 1] - sh.f_uoff[i];
+        if (lane < Gr[i]) x[i] = P[sh.f_uoff[i] + lane];
+      } else if (i == nsamp && i < nr) {  // the exact round
+        Gr[i] = 32;
+        float e = 0.0f;
         if (a.vec) {
           for (int j = lane * 4; j < m; j += 128) {
             const float4 d4 = *reinterpret_cast<const float4*>(row + j);
-            x = add_term<L1>(d4.x, x);
-            x = add_term<L1>(d4.y, x);
-            x = add_term<L1>(d4.z, x);
-            x = add_term<L1>(d4.w, x);
+            e = add_term<L1>(d4.x, e);
+            e = add_term<L1>(d4.y, e);
+            e = add_term<L1>(d4.z, e);
+            e = add_term<L1>(d4.w, e);
           }
         } else {
-          for (int j = lane; j < m; j += 32) x = add_term<L1>(row[j], x);
+          for (int j = lane; j < m; j += 32) e = add_term<L1>(row[j], e);
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      } else {
-        const int G = sh.f_uoff[i + 1] - sh.f_uoff[i];
-        if (lane < G) x = P[sh.f_uoff[i] + lane];
-#pragma unroll
-        for (int o = 16; o; o >>= 1)
-          if (o < G) x += __shfl_xor_sync(0xffffffffu, x, o);
+        x[i] = e;
       }
-      if (lane == 0) {
-        if (i == 0) {  // this round: Kahan-compensated running sum, as a gather updates it
-          const float S0 = Sc[s], c0 = Cc[s];
-          const float y = x - c0;
-          const float tt = S0 + y;
-          Cc[s] = (tt - S0) - y;
-          Sc[s] = tt;
-          atomicAdd(&hist[f2key(tt) >> 20], 1u);
-        } else {
-          F[(size_t)(i - 1) * (size_t)cap + s] = x;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+      for (int i = 0; i < kFuseRounds; ++i) {
+        if (i < nr) {
+          const float y = __shfl_xor_sync(0xffffffffu, x[i], o);
+          if (o < Gr[i]) x[i] += y;
         }
       }
+    }
+    if (lane == 0) {
+      {  // this round: Kahan-compensated running sum, as a gather updates it
+        const float S0 = Sc[s], c0 = Cc[s];
+        const float y = x[0] - c0;
+        const float tt = S0 + y;
+        Cc[s] = (tt - S0) - y;
+        Sc[s] = tt;
+        atomicAdd(&hist[f2key(tt) >> 20], 1u);
+      }
+#pragma unroll
+      for (int i = 1; i < kFuseRounds; ++i)
+        if (i < nr) F[(size_t)(i - 1) * (size_t)cap + s] = x[i];
     }
     __syncwarp();
   }
