@@ -98,7 +98,8 @@ struct AdaptiveArgs {
   const int32_t* qorder = nullptr;  // order in which CTAs take the queries (null: batch order)
   int32_t r0_resum = 0; // the round-0 sums came from the tensor-core contraction: the points the
                         // round-0 filter keeps get their sums again, sample by sample
-  float* ws_F = nullptr;  // row passes: later rounds' sums per active slot, [2][kFuseRounds][fuse_cap] per CTA
+  float* ws_F = nullptr;  // row passes: later rounds' sums by pass slot, [kFuseRounds][fuse_cap] per CTA,
+                          // then each active slot's pass slot, [2][fuse_cap] (int32)
   int32_t fuse_cap = 0;   // slots a row pass may cover (0: no row passes)
 };
 
@@ -816,13 +817,13 @@ __device__ __forceinline__ void gather_fused(const AdaptiveArgs& a, const Adapti
   }
 }
 
-// A round whose sums a row pass formed: the running sums take them as a
-// gather would (exact rounds replace them).
+// A round whose sums a row pass formed (read through each slot's pass slot):
+// the running sums take them as a gather would (exact rounds replace them).
 template <int NT>
-__device__ __forceinline__ void gather_from_pass(int nact, bool exact, const float* Fc, float* Sc, float* Cc,
-                                                 uint32_t* hist) {
+__device__ __forceinline__ void gather_from_pass(int nact, bool exact, const float* Fc, const int32_t* fslot,
+                                                 float* Sc, float* Cc, uint32_t* hist) {
   for (int s = threadIdx.x; s < nact; s += NT) {
-    const float x = Fc[s];
+    const float x = Fc[fslot[s]];
     float S;
     if (exact) {
       S = x;
@@ -952,8 +953,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
   float* acc_U = a.ws_acc_U + slot * (size_t)a.acc_cap;
   float* acc_L = a.ws_acc_L + slot * (size_t)a.acc_cap;
   // row passes: sums of later rounds per active slot, ping-pong like the slots
-  float* const F0 = a.ws_F ? a.ws_F + slot * 2 * kFuseRounds * (size_t)a.fuse_cap : nullptr;
-  auto Fcol = [&](int b, int c) { return F0 + ((size_t)b * kFuseRounds + c) * (size_t)a.fuse_cap; };
+  // row passes: round c's sums by pass slot (the slot a point had in the pass
+  // round), and each active slot's pass slot, ping-pong like the slots
+  float* const F0 = a.ws_F ? a.ws_F + slot * (kFuseRounds + 2) * (size_t)a.fuse_cap : nullptr;
+  auto Fcol = [&](int c) { return F0 + (size_t)c * (size_t)a.fuse_cap; };
+  auto Fslot = [&](int b) { return reinterpret_cast<int32_t*>(F0 + (size_t)(kFuseRounds + b) * (size_t)a.fuse_cap); };
   KNN_PHASE_START;
 
   for (;;) {
@@ -1033,7 +1037,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
     }
 
     int nact = (int)n, nacc = 0, cur = 0, r = 0, term = 0;
-    int fcols = 0, nact_prev = 0;  // rounds held in F; active points at the previous round's start
+    int fcols = 0, fnext = 0, nact_prev = 0;  // rounds held in F, the next one's column; active points at
+                                               // the previous round's start
     int64_t T = 0, evals = 0;
     float min_elim = INFINITY;
     for (;;) {
@@ -1102,13 +1107,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       __syncthreads();
       KNN_PHASE(0);  // setup
       // slots' sums of later rounds to carry through this round's compaction
-      int fsrc = 0, fmove = 0;
-      if (fuse_now) {
-        fmove = sh.f_nr - 1;
-      } else if (fcols > 0) {
-        fsrc = 1;
-        fmove = fcols - 1;
-      }
+      // a pass slot to carry through this round's compaction: the pass round
+      // gives each slot its own; later rounds carry them while F holds rounds
+      const int fcarry = fuse_now ? 1 : (fcols > 1 ? 2 : 0);
       if (flt) {
         nact = round0_filter<NT>(a, q, n, k, w, Tf, hist, buf, sh, ids0 + (size_t)cur * n, Sc,
                                  ids0 + (size_t)(cur ^ 1) * n, S0 + (size_t)(cur ^ 1) * n, lcode, lS, &min_elim);
@@ -1123,9 +1124,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
         }
       }
       else if (kRowPass && fcols > 0)  // a row pass formed this round's sums
-        gather_from_pass<NT>(nact, exact, Fcol(cur, 0), Sc, Cc, hist);
+        gather_from_pass<NT>(nact, exact, Fcol(fnext), Fslot(cur), Sc, Cc, hist);
       else if (kRowPass && fuse_now)
-        gather_fused<NT, L1>(a, sh, qid, nact, qs, idc, Sc, Cc, hist, frows, Fcol(cur, 0));
+        gather_fused<NT, L1>(a, sh, qid, nact, qs, idc, Sc, Cc, hist, frows, Fcol(0));
       else if (exact)  // the exact cap reads the FP32 data whatever copy the samples use
         gather_exact<NT, L1>(a, r, nact, qs, idc, Sc, hist);
       else if (pre)
@@ -1220,8 +1221,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
             idn[pos] = myid[e];
             Sn[pos] = myS[e];
             Cn[pos] = myC[e];
-            if constexpr (kRowPass)
-              for (int c = 0; c < fmove; ++c) Fcol(cur ^ 1, c)[pos] = Fcol(cur, fsrc + c)[cb + tid * kIPT + e];
+            if constexpr (kRowPass) {
+              if (fcarry) {
+                const int sl = cb + tid * kIPT + e;
+                Fslot(cur ^ 1)[pos] = fcarry == 1 ? sl : Fslot(cur)[sl];
+              }
+            }
             ++pos;
           }
         }
@@ -1232,7 +1237,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) adaptive_rounds_kernel(Adaptive
       nacc = min(nacc + sh.nacc_add, a.acc_cap);
       nact_prev = nact;
       nact = out_base;
-      fcols = fmove;
+      if (fuse_now) {
+        fcols = sh.f_nr - 1;
+        fnext = 0;
+      } else if (fcols > 0) {
+        --fcols;
+        ++fnext;
+      }
       min_elim = fminf(min_elim, rmin);
       T = Tn;
       cur ^= 1;
@@ -1821,7 +1832,7 @@ static size_t carve_adaptive(Carve& cv, int64_t n, const AdaptivePlan& p, Adapti
   c.acc_d = cv.take<float>(acc);
   c.acc_U = cv.take<float>(acc);
   c.acc_L = cv.take<float>(acc);
-  c.F = p.fuse_cap ? cv.take<float>((size_t)p.grid * 2 * kFuseRounds * (size_t)p.fuse_cap) : nullptr;
+  c.F = p.fuse_cap ? cv.take<float>((size_t)p.grid * (kFuseRounds + 2) * (size_t)p.fuse_cap) : nullptr;
   if (out) *out = c;
   return cv.off;
 }
