@@ -59,17 +59,20 @@ C_GRID = [1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5]
 RECALL_TARGET = 0.999
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# round-loop kernel in one adaptive call on this workload, from one ncu
-# capture per schedule the autotuner picks (profiles/), with the kernel's
-# time from the library's CUDA events. A record is reported only while the
+# round-loop kernel and of the point-major round-0 pass in one adaptive call
+# on this workload, from one ncu capture per kernel and schedule the
+# autotuner picks (profiles/), with the kernels' times from the library's
+# CUDA events. A record is reported only while the
 # kernel sources hash to the recorded value and the launch configuration
 # matches; otherwise the roofline's traffic is null.
-TRAFFIC_CAPTURE = {"sha1": "72bd7ffcc9078d6d6dff791d2ed6f37faf6150f4",
+TRAFFIC_CAPTURE = {"sha1": "b0b5022adf756ab64b778ca89f450062cec1063c",
                    "records": [
                        {"config": {"c_alpha": 1e-3, "B0": 8, "B": 8, "grow": 1, "threads": 1024, "nq": 1024},
-                        "rounds_bytes": 14.037e9 + 1.097e9, "rounds_ms": 4.46},
+                        "rounds_bytes": 9.095e9 + 0.796e9, "rounds_ms": 4.34,
+                        "round0_bytes": 0.317e9 + 0.363e9, "round0_ms": 1.27},
                        {"config": {"c_alpha": 3e-4, "B0": 16, "B": 16, "grow": 1, "threads": 1024, "nq": 1024},
-                        "rounds_bytes": 4.686e9 + 0.336e9, "rounds_ms": 2.72},
+                        "rounds_bytes": 1.546e9 + 0.094e9, "rounds_ms": 2.04,
+                        "round0_bytes": 0.317e9 + 0.367e9, "round0_ms": 2.12},
                    ]}
 # Schedule of the oracle runs when no GPU line gives one (the autotuner's
 # usual choice on this workload).
@@ -101,6 +104,30 @@ def kernel_sources_sha1():
         text = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
         h.update(text.encode())
     return h.hexdigest()
+
+
+def philox_rate(knn, torch, dev, sms, iters=2048):
+    """Philox4x32-10 blocks per second (G/s) this GPU sustains with the
+    library's generator function (knn_philox_blocks), two 1024-thread CTAs
+    per SM, timed with CUDA events after two warm-up launches."""
+    ctas = 2 * sms
+    out = torch.empty(ctas * 1024, dtype=torch.int32, device=dev)
+    for _ in range(2):
+        knn.philox_blocks(iters, ctas, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        knn.philox_blocks(iters, ctas, out)
+    e1.record()
+    torch.cuda.synchronize()
+    return ctas * 1024 * iters / (e0.elapsed_time(e1) / 3 / 1e3) / 1e9
+
+
+def alu_peak_blocks(sms, sm_max_mhz):
+    """Philox4x32-10 blocks per second (G/s) at the integer-multiply rate:
+    an SM issues 64 32-bit multiply-adds per clock (16 per scheduler), a
+    block takes 40 (10 rounds, two products, high and low words each)."""
+    return sms * 64 * sm_max_mhz * 1e6 / 40 / 1e9
 
 
 def peaks():
@@ -333,7 +360,15 @@ def run_ours(args, rank, world, local_rank):
     cfg_now = {"c_alpha": chosen, "B0": B0, "B": B, "grow": grow, "threads": best["threads"], "nq": nq}
     rec_now = traffic_record(cfg_now)
     traffic = rec_now["rounds_bytes"] if rec_now else None
+    traffic_r0 = rec_now["round0_bytes"] if rec_now else None
     sector_gbs = 32 * evals / (kern_ms / 1e3) / 1e9
+    # The round-0 pass is bound by the integer multiplies of Philox4x32-10
+    # (two blocks per 8 draws of a pair): its roofline counts blocks against
+    # the multiply rate of the SMs at their maximum clock.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    r0_blocks = nq * n * 2 * (-(-B0 // 8)) if r0_evals else 0
+    alu_peak = alu_peak_blocks(sms, clk.get("sm_max_mhz") or 2070.0)
+    alu_probe = philox_rate(knn, torch, dev, sms)
 
     # ---- recall of the timed batch against the exact method
     ti, td = ds.exact(Qd, k, screen="f32")
@@ -601,6 +636,32 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - e2e_t0) * 1e3 / e2e_steps)
 
+    hbm_rounds = {
+        "bound": "hbm", "kernel": f"adaptive_rounds_kernel<{best['threads']}, ElemF32>",
+        "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 5),
+        "traffic": traffic, "peak_kind": peak_kind, "kernel_ms": round(loop_kern_ms, 4),
+        "alg_bytes_per_launch": alg_bytes,
+        "dram_gbs": round(traffic / (loop_kern_ms / 1e3) / 1e9, 2) if traffic else None,
+        "dram_frac": round(traffic / (loop_kern_ms / 1e3) / 1e9 / hbm, 5) if traffic else None,
+        "note": "algorithmic bytes = 4 B (FP32 element) per coordinate evaluation after round 0 plus the "
+                "round-0 sums read (4 B per pair), over the kernel's time from the library's CUDA events on the "
+                "launching stream (mean of 3 calls); row passes read each active row once, so DRAM carries "
+                "less than the algorithmic bytes"}
+    alu_round0 = {
+        "bound": "alu", "kernel": "round0_kernel<ElemF32>",
+        "achieved": round(r0_blocks / (r0_kern_ms / 1e3) / 1e9, 2) if r0_kern_ms else None,
+        "peak": round(alu_peak, 2), "unit": "G Philox4x32-10 blocks/s",
+        "frac": round(r0_blocks / (r0_kern_ms / 1e3) / 1e9 / alu_peak, 5) if r0_kern_ms else None,
+        "traffic": traffic_r0, "kernel_ms": round(r0_kern_ms, 4), "blocks_per_launch": r0_blocks,
+        "peak_kind": "derived: SMs x 64 int32 multiply-adds per clock x max SM clock / 40 per block",
+        "peak_probe": round(alu_probe, 2),
+        "hbm_alg_gbs": round(4 * r0_evals / (r0_kern_ms / 1e3) / 1e9, 2) if r0_kern_ms else None,
+        "note": "a pair's round 0 takes 2 ceil(B0/8) blocks (4 draws each); peak_probe = blocks/s of "
+                "knn_philox_blocks on this GPU; hbm_alg_gbs = 4 B per round-0 evaluation over the kernel's time"}
+    for r in (hbm_rounds, alu_round0):
+        r["traffic_source"] = ("recorded ncu capture of this kernel source and launch configuration "
+                               "(dram__bytes_read.sum + dram__bytes_write.sum, one call); null when either "
+                               "changed") if r["traffic"] else None
     result = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -639,26 +700,11 @@ def run_ours(args, rank, world, local_rank):
                            "agrees_with_simt_path": exact_agree,
                            "simt_f32_screen": {"queries_per_s": round(world * nq / (exact_simt_ms / 1e3), 3),
                                                "ms_per_batch": round(exact_simt_ms, 4)}},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 5), "traffic": traffic,
-                     "traffic_source": "recorded ncu capture of this kernel source and launch configuration "
-                                       "(dram__bytes_read.sum + dram__bytes_write.sum of the round-loop kernel, "
-                                       "one call); null when either changed" if traffic else None,
-                     "dram_gbs": round(traffic / (loop_kern_ms / 1e3) / 1e9, 2) if traffic else None,
-                     "dram_frac": round(traffic / (loop_kern_ms / 1e3) / 1e9 / hbm, 5) if traffic else None,
-                     "kernel": f"adaptive_rounds_kernel<{best['threads']}, ElemF32>",
-                     "kernel_ms": round(loop_kern_ms, 4),
-                     "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
-                     "call": {"kernels": "round0_kernel<ElemF32> + adaptive_rounds_kernel", "ms": round(kern_ms, 4),
-                              "round0_ms": round(r0_kern_ms, 4), "alg_bytes": alg_bytes_call,
-                              "frac": round(alg_bytes_call / (kern_ms / 1e3) / 1e9 / hbm, 5),
-                              "alg_bytes_builder": alg_bytes_builder},
-                     "sector_gbs": round(sector_gbs, 2),
-                     "note": "algorithmic bytes = 4 B (FP32 element) per coordinate evaluation: the round loop "
-                             "reads those of the rounds after round 0 plus the round-0 sums (4 B per pair); "
-                             "achieved = those bytes / the round-loop kernel's time from the library's CUDA events "
-                             "on the launching stream (mean of 3 calls); call = both kernels, 4 B per evaluation; "
-                             "sector_gbs counts 32 B per evaluation (the DRAM granule a random 4-byte gather moves)"},
+        "roofline": roofline_of(hbm_rounds, alu_round0, r0_kern_ms, loop_kern_ms,
+                                {"kernels": "round0_kernel<ElemF32> + adaptive_rounds_kernel", "ms": round(kern_ms, 4),
+                                 "alg_bytes": alg_bytes_call,
+                                 "frac": round(alg_bytes_call / (kern_ms / 1e3) / 1e9 / hbm, 5),
+                                 "alg_bytes_builder": alg_bytes_builder, "sector_gbs": round(sector_gbs, 2)}),
         "e2e": {"value": round(world * nq / (e2e_ms / 1e3), 3), "unit": "queries/s",
                 "h2d_bytes_per_step": nq * m * 4, "d2h_bytes_per_step": nq * k * 16},
         "gpu_launches": launches_per_step * args.steps,
@@ -666,6 +712,15 @@ def run_ours(args, rank, world, local_rank):
         "_traces": traced,
     }
     return result
+
+
+def roofline_of(hbm_rounds, alu_round0, r0_ms, loop_ms, call):
+    """The line's roofline: the dominant kernel's (the longer of the two),
+    with both kernels' under "kernels" and the whole call under "call"."""
+    top = dict(alu_round0 if r0_ms >= loop_ms else hbm_rounds)
+    top["kernels"] = {"round0_kernel": alu_round0, "adaptive_rounds_kernel": hbm_rounds}
+    top["call"] = call
+    return top
 
 
 def oracle_schedule(args, cfg=None):

@@ -392,6 +392,15 @@ knn_status knn_phase_clocks(uint64_t* out, int32_t reset);
 knn_status knn_kernel_timing(int32_t enable);
 knn_status knn_kernel_times(double* out_ms, int32_t reset);
 
+/* Rate of the coordinate generator (measurement; no counterpart in the
+ * paper): ctas CTAs of 1024 threads each evaluate iters Philox4x32-10 blocks
+ * with the kernels' own generator function and write one word per thread to
+ * out (device, ctas * 1024 uint32, caller-owned). Time it on `stream` to
+ * measure the blocks per second this GPU sustains; every draw of the
+ * per-pair estimator costs a quarter of a block. KNN_EINVAL on iters < 0,
+ * ctas < 1 or a null out. */
+knn_status knn_philox_blocks(int64_t iters, int32_t ctas, uint32_t* out, void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* knn_last_error(void);
 

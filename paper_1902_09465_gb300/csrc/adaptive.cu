@@ -316,3 +316,27 @@ extern "C" knn_status knn_adaptive_noalloc(const float* X, int64_t n, int32_t m,
   set_blocks<ElemF32>(a, o);
   return launch_rounds<ElemF32>(p, a, stream);
 }
+
+// --------------------------------------------------------- generator rate
+namespace knn {
+// Each thread evaluates `iters` Philox4x32-10 blocks with the round loop's
+// generator (counter: block index, thread, two fixed words; the round keys of
+// a fixed seed) and writes the XOR of their words, so that none is dropped.
+static __global__ void __launch_bounds__(1024) philox_blocks_kernel(PhiloxKeys K, int64_t iters, uint32_t* out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (int64_t i = 0; i < iters; ++i) {
+    const uint4 w = philox4x32_10_rk((uint32_t)i, t, 0x9E3779B9u, 0x7F4A7C15u, K);
+    acc += w.x ^ w.y ^ w.z ^ w.w;
+  }
+  out[t] = acc;
+}
+}  // namespace knn
+
+extern "C" knn_status knn_philox_blocks(int64_t iters, int32_t ctas, uint32_t* out, void* stream) {
+  knn::clear_error();
+  if (iters < 0 || ctas < 1 || !out) return knn::set_error("knn_philox_blocks: bad arguments"), KNN_EINVAL;
+  knn::philox_blocks_kernel<<<ctas, 1024, 0, static_cast<cudaStream_t>(stream)>>>(knn::philox_keys(0x243F6A8885A308D3ull),
+                                                                                   iters, out);
+  return knn::cuda_check(cudaGetLastError(), "philox_blocks_kernel launch");
+}

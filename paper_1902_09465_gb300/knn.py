@@ -70,6 +70,7 @@ _SIGS = {
     "knn_adaptive_ds_multi": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_double, C.c_uint64,
                                         C.POINTER(Opts), _P, _P, _P, _P, _P, C.c_size_t, _P]),
     "knn_dataset_share": (C.c_int, [_P, C.c_uint64, C.c_int32, _P]),
+    "knn_philox_blocks": (C.c_int, [C.c_int64, C.c_int32, _P, _P]),
     "knn_last_error": (C.c_char_p, []),
     "knn_version": (C.c_char_p, []),
 }
@@ -386,6 +387,14 @@ def kernel_times(reset: bool = True):
     out = (C.c_double * 2)()
     _check(lib().knn_kernel_times(out, 1 if reset else 0))
     return float(out[0]), float(out[1])
+
+
+def philox_blocks(iters: int, ctas: int, out: torch.Tensor, stream=None) -> None:
+    """knn_philox_blocks: ctas x 1024 threads each evaluate `iters` blocks of
+    the coordinate generator; out is an int32 CUDA tensor of ctas*1024."""
+    if out.numel() < ctas * 1024:
+        raise KnnError("out holds fewer than ctas * 1024 words")
+    _check(lib().knn_philox_blocks(int(iters), int(ctas), _dev(out, "out", torch.int32), _stream(stream)))
 
 
 def device_status() -> int:

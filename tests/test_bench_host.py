@@ -93,3 +93,18 @@ def test_cpu_baseline_reports_model_and_single_core_rate():
     assert isinstance(r["cpu_model"], str) and r["cpu_model"]
     st = r["single_thread"]
     assert st["cores"] == 1 and st["value"] > 0 and "queries" in st["sample"]
+
+
+def test_roofline_picks_the_longer_kernel_and_keeps_both():
+    hbm = {"bound": "hbm", "kernel": "rounds"}
+    alu = {"bound": "alu", "kernel": "round0"}
+    r = bench.roofline_of(hbm, alu, 2.1, 2.0, {"ms": 4.1})
+    assert r["bound"] == "alu" and r["kernel"] == "round0"
+    assert r["kernels"] == {"round0_kernel": alu, "adaptive_rounds_kernel": hbm} and r["call"] == {"ms": 4.1}
+    r = bench.roofline_of(hbm, alu, 1.0, 2.0, {})
+    assert r["bound"] == "hbm" and r["kernel"] == "rounds"
+
+
+def test_alu_peak_counts_forty_multiplies_per_block():
+    # 152 SMs x 64 multiply-adds per clock x 2.07 GHz / 40 = 503.4 G blocks/s
+    assert abs(bench.alu_peak_blocks(152, 2070.0) - 503.424) < 1e-3
