@@ -41,7 +41,8 @@ extern "C" size_t knn_adaptive_workspace_size(int64_t n, int32_t m, int32_t nq, 
   if (round0_applies(m, o) || (o.block <= 1 && o.B0 < m && o.B0 <= 64)) {  // dataset paths only
     const size_t chunk = (size_t)round0_chunk(n, nq, p.grid);
     cv.take<float>(chunk * (size_t)n);                                      // round-0 sums
-    cv.take<float>(chunk * (size_t)((n + round0_rows(m) - 1) / round0_rows(m)));  // their tile minima
+    const int64_t rows = round0_rows(m, o.B0);
+    cv.take<float>(chunk * (size_t)std::max<int64_t>((n + rows - 1) / rows, (n + 31) / 32));  // their tile minima
     cv.take<float>(chunk * 64);                                             // permuted query columns
     if (o.r0_tensor && o.B0 <= 64) cv.take<uint8_t>(round0_tc_scratch(n, (int32_t)chunk));  // tensor-core round 0
   }

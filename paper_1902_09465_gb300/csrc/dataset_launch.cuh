@@ -32,7 +32,7 @@ knn_status adaptive_ds_launch(const knn_dataset* ds, const float* Q, int32_t nq,
   if (s != KNN_OK) return s;
   const int chunk = r0 ? round0_chunk(n, nq, p.grid) : nq;
   // round-0 tile minima: per CTA of the staged-rows pass, per warp of the shared pass
-  const int rows = round0_rows(m);
+  const int rows = round0_rows(m, o.B0);
   const int tiles = !r0 ? 0 : (int)(E::kPerm ? (n + 31) / 32 : (n + rows - 1) / rows);
   Carve measure;
   carve_adaptive(measure, n, p, nullptr);
