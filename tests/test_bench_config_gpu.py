@@ -3,7 +3,8 @@
 Workload: pixel mixture, n = 100,000 points in d = 784, 1,024 queries, k = 10,
 delta = 0.01 (the inputs bench.py generates). Path: a resident dataset, the
 point-major round-0 pass and the round-0 filter, rounds B0 = B = 8 (C_alpha
-= 1e-3) or 16 (C_alpha = 3e-4) doubling -- the autotuner's choices --,
+= 1e-3) or 16 (C_alpha = 3e-4) doubling, or B0 = 16 then the exact distance
+-- the autotuner's choices --,
 1,024 threads per query, the Section 5 bound, rounds and
 FP64 rerank captured in one CUDA graph (runtime.GraphStep) — the step bench.py
 times. Sampled queries (first, middle, last, and two more) then run alone
@@ -30,7 +31,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # the two schedules the benchmark's autotuner has chosen on this workload
 # (its choice follows the measured rates, so both are replayed)
 SCHEDULES = [dict(bound="exp", c_alpha=1e-3, B0=8, B=8, grow=1, threads=1024),
-             dict(bound="exp", c_alpha=3e-4, B0=16, B=16, grow=1, threads=1024)]
+             dict(bound="exp", c_alpha=3e-4, B0=16, B=16, grow=1, threads=1024),
+             dict(bound="exp", c_alpha=3e-4, B0=16, B=runtime.EXACT_NEXT, grow=0, threads=1024)]
 
 
 @pytest.mark.parametrize("BENCH_OPTS", SCHEDULES)
