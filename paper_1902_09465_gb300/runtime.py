@@ -80,8 +80,7 @@ def recall(got_idx, got_dist, true_idx, true_dist, rel: float = 1e-6) -> float:
 # B past any row length: the round after round 0 is the exact distance (the
 # exact cap at T + B >= m), so the points round 0 keeps are computed in full
 EXACT_NEXT = 1 << 20
-DEFAULT_SCHEDULES = ((16, 16, 1), (8, 8, 1), (32, 32, 1), (16, 16, 0), (32, 16, 0), (16, EXACT_NEXT, 0),
-                     (32, EXACT_NEXT, 0))
+DEFAULT_SCHEDULES = ((16, 16, 1), (8, 8, 1), (32, 32, 1), (16, 16, 0), (16, EXACT_NEXT, 0), (32, EXACT_NEXT, 0))
 BLOCK_SCHEDULES = ((2, 2, 1), (4, 4, 1), (8, 8, 1))  # in blocks of coordinates
 DEFAULT_C_GRID = (1e-1, 3e-2, 1e-2, 3e-3, 1e-3, 3e-4, 1e-4, 3e-5)
 

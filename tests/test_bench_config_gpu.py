@@ -28,8 +28,8 @@ from paper_1902_09465_gb300 import knn, runtime
 pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-# the two schedules the benchmark's autotuner has chosen on this workload
-# (its choice follows the measured rates, so both are replayed)
+# the schedules the benchmark's autotuner has chosen on this workload
+# (its choice follows the measured rates, so each is replayed)
 SCHEDULES = [dict(bound="exp", c_alpha=1e-3, B0=8, B=8, grow=1, threads=1024),
              dict(bound="exp", c_alpha=3e-4, B0=16, B=16, grow=1, threads=1024),
              dict(bound="exp", c_alpha=3e-4, B0=16, B=runtime.EXACT_NEXT, grow=0, threads=1024)]
