@@ -73,6 +73,9 @@ TRAFFIC_CAPTURE = {"sha1": "7011a26cc8f8ae147e5719503a624eba7b2303e3",
                        {"config": {"c_alpha": 3e-4, "B0": 16, "B": 16, "grow": 1, "threads": 1024, "nq": 1024},
                         "rounds_bytes": 1.550e9 + 0.097e9, "rounds_ms": 2.04,
                         "round0_bytes": 0.317e9 + 0.363e9, "round0_ms": 2.02},
+                       {"config": {"c_alpha": 3e-4, "B0": 16, "B": 1 << 20, "grow": 0, "threads": 1024, "nq": 1024},
+                        "rounds_bytes": 1.361e9 + 0.076e9, "rounds_ms": 0.676,
+                        "round0_bytes": 0.317e9 + 0.362e9, "round0_ms": 2.02},
                    ]}
 # Schedule of the oracle runs when no GPU line gives one (the autotuner's
 # usual choice on this workload).
