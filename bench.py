@@ -20,7 +20,10 @@ is the maximum over ranks.
 The same line reports the variants beside the headline: stored BF16 / FP8
 copies, shared coordinates, 32-byte block samples and draws without
 replacement, each autotuned the same way; the exact method with every screen;
-the roofline of the adaptive call; the path end to end from pinned host
+the roofline of the adaptive call's longer kernel (the point-major round-0
+pass against the integer-multiply peak of its Philox blocks, or the round
+loop on algorithmic bytes), both kernels' under roofline.kernels; the path
+end to end from pinned host
 buffers; a serving leg (Poisson arrivals, continuous batching, request
 latency); small batches of 1, 8 and 64 queries; and the oracle on this
 host's cores, which also replays traced queries of the batch to report the
@@ -30,7 +33,8 @@ estimates' errors against FP64.
 queries) on a bounded sample of the same workload on this host's cores.
 Other modes: --sweep (gap-ratio precision sweep), --figure2 (Section 5's
 C_alpha sweep), --serve (the request loop), --profile-step (the timed step
-alone, for profilers; --phases adds the phase-timing build's clock shares;
+alone, for profilers; --phases adds the phase-timing build's clock shares,
+--no-row-pass turns row passes off;
 --share --r0-tensor the shared-coordinate step with the tensor-core round 0),
 --profile-exact (the exact method alone, --screen f16 | bf16 | bf16x3).
 """
