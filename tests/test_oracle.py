@@ -517,3 +517,23 @@ def test_copy_width_in_round_0_uses_the_active_estimates(target, decided):
         assert np.all(rounds == 0) and np.all((r["code"][0][1:] & 3) == oracle.ELIMINATED)
     else:
         assert r["stats"][0]["rounds"] >= 2 and np.all(rounds[:3] >= 1)
+
+
+def test_batch_past_m_is_round_0_then_exact_distances():
+    """A later-round batch past m (the exact cap T + B >= m): a point is
+    decided in round 0 (T = B0) or ends at T = m with its sum the exact
+    squared distance and m evaluations more; the planted nearest, kept by
+    round 0, are returned."""
+    n, m, k = 2000, 96, 5
+    X, Q, _ = synth.gaussian_planted(n, m, k, seed=11)
+    r = oracle.adaptive(X, Q, _params(k=k, B0=16, B=1 << 20, grow=0, c_alpha=1e-3))
+    st = r["stats"][0]
+    T = r["T"][0]
+    assert st["rounds"] <= 2 and set(np.unique(T).tolist()) <= {16, m}
+    full = T == m
+    assert 0 < full.sum() < n
+    d = ((X.astype(np.float64) - Q[0].astype(np.float64)) ** 2).sum(axis=1)
+    np.testing.assert_allclose(r["S"][0][full], d[full], rtol=1e-12)
+    assert st["evals"] == n * 16 + int(full.sum()) * m
+    ti, _ = oracle.exact_knn(X, Q[:1], k)
+    assert set(ti[0].tolist()) <= set(r["idx"][0][: st["count"]].tolist())
