@@ -870,45 +870,91 @@ __device__ int round0_filter(const AdaptiveArgs& a, int q, int64_t n, int k, flo
   const float Sc = __uint_as_float(lo);
   for (int i = tid; i < kHistBins; i += NT) hist[i] = 0;
   __syncthreads();
-  // warp w scans its own contiguous segment, U loads in flight per lane;
-  // ballots keep the order inside the warp, the warps' counts the order across
+  // warp w scans its own contiguous segment, several loads in flight per
+  // lane; the kept points are staged in index order (ballots or a warp scan
+  // inside the warp, the warps' counts across them)
   constexpr int U = 8;
   constexpr int NW = NT / 32;
-  const int64_t seg = ((n + NW - 1) / NW + 31) & ~(int64_t)31;
-  const int64_t s0 = (int64_t)warp * seg, s1 = min(n, s0 + seg);
   const float* R0q = a.R0 + (size_t)q * (size_t)n;
+  // 16-byte loads when the rows of sums are 16-byte aligned: segments of a
+  // multiple of 128 sums, four per lane and load, U4 loads in flight
+  const bool vec4 = (n & 3) == 0 && ((reinterpret_cast<uintptr_t>(a.R0) & 15) == 0);
+  const int64_t seg = vec4 ? ((n + NW - 1) / NW + 127) & ~(int64_t)127 : ((n + NW - 1) / NW + 31) & ~(int64_t)31;
+  const int64_t s0 = (int64_t)warp * seg, s1 = min(n, s0 + seg);
   int cnt = 0;
   float mn = INFINITY;  // smallest dropped sum
-  for (int64_t base = s0; base < s1; base += 32 * U) {
-    float v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = base + u * 32 + lane;
-      v[u] = i < s1 ? __ldcs(R0q + i) : 0.0f;
+  auto drop = [&](int64_t i, float v) {  // LCB > tU
+    mn = fminf(mn, v);
+    if (lcode) {
+      lcode[i] = 1;  // eliminated in round 0
+      if (lS) lS[i] = v;
     }
+  };
+  if (vec4) {
+    constexpr int U4 = 4;
+    for (int64_t base = s0; base < s1; base += 128 * U4) {
+      float4 v[U4];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = base + u * 32 + lane;
-      bool keep = false;
-      if (i < s1) {
-        if (v[u] > Sc) {  // LCB > tU
-          mn = fminf(mn, v[u]);
-          if (lcode) {
-            lcode[i] = 1;  // eliminated in round 0
-            if (lS) lS[i] = v[u];
+      for (int u = 0; u < U4; ++u) {
+        const int64_t i = base + u * 128 + 4 * lane;  // s1 is a multiple of 4: a float4 is in or out
+        v[u] = i < s1 ? __ldcs(reinterpret_cast<const float4*>(R0q + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U4; ++u) {
+        const int64_t i = base + u * 128 + 4 * lane;
+        const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        uint32_t km = 0;
+        if (i < s1) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (vv[c] > Sc) drop(i + c, vv[c]); else km |= 1u << c;
           }
-        } else {
-          keep = true;
         }
+        // kept sums of lower lanes come first (index order: lane, then c)
+        const int kc = __popc(km);
+        int incl = kc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        int pos = cnt + incl - kc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (km & (1u << c)) {
+            stI[s0 + pos] = (int32_t)(i + c);
+            stS[s0 + pos] = vv[c];
+            atomicAdd(&hist[f2key(vv[c]) >> 20], 1u);
+            ++pos;
+          }
+        }
+        cnt += __shfl_sync(0xffffffffu, incl, 31);
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-        stI[s0 + pos] = (int32_t)i;
-        stS[s0 + pos] = v[u];
-        atomicAdd(&hist[f2key(v[u]) >> 20], 1u);
+    }
+  } else {
+    for (int64_t base = s0; base < s1; base += 32 * U) {
+      float v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = base + u * 32 + lane;
+        v[u] = i < s1 ? __ldcs(R0q + i) : 0.0f;
       }
-      cnt += __popc(bal);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = base + u * 32 + lane;
+        bool keep = false;
+        if (i < s1) {
+          if (v[u] > Sc) drop(i, v[u]); else keep = true;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+          stI[s0 + pos] = (int32_t)i;
+          stS[s0 + pos] = v[u];
+          atomicAdd(&hist[f2key(v[u]) >> 20], 1u);
+        }
+        cnt += __popc(bal);
+      }
     }
   }
   int total;
